@@ -1,0 +1,92 @@
+/*
+ * vcm_oracle.h -- plain, slow CPU oracle for the visibility color map (VCM).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this library.  The GPU library shares no
+ * code, header, table or helper with it.
+ *
+ * What it computes (target-centric VCM, Def. 1 of Section II-A):
+ *   - the target is an axis-aligned rectangle (3D) or segment (2D) split into
+ *     patches_u x patches_w patches whose centres are the sample points
+ *     (a cell is represented by its centre, Section III-A end);
+ *   - a viewpoint q sees patch centre p iff the closed segment qp meets no
+ *     obstacle box (point-to-point visibility, Def. 2 of Section II-B.2; a
+ *     segment that only touches a box is blocked, Def. 4 of Section III-B);
+ *   - the visibility is the sum over visible patches of A*cos(theta)/d^2 (3D,
+ *     the solid angle of the visible part) or len*cos(theta)/d (2D, the
+ *     subtended angle, which reduces to Eq. 1 of Section II-B.1 for an
+ *     unobstructed target seen head-on);
+ *   - colors are the visibility normalised to [0,1] (Def. 1) and cut into
+ *     L levels, with level 0 reserved for zero visibility (Section III-C).
+ *
+ * Lengths are integer lattice units of 2^-10 m; every coordinate must satisfy
+ * |x| <= 2^24 units.  Occlusion is decided in exact int64 arithmetic; the
+ * measure is summed in float64 with Neumaier compensation.
+ *
+ * Axis codes: 0 = +x, 1 = -x, 2 = +y, 3 = -y, 4 = +z, 5 = -z.
+ */
+#ifndef VCM_ORACLE_H
+#define VCM_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t dims;        /* 2 or 3 */
+    int64_t n_boxes;
+    const int64_t *lo;   /* [n_boxes][3], lattice units (z ignored in 2D) */
+    const int64_t *hi;   /* [n_boxes][3] */
+} vo_scene;
+
+typedef struct {
+    int32_t dims;
+    int64_t center[3];
+    int32_t axis_u, axis_w, normal;   /* axis codes; axis_w unused in 2D */
+    int64_t width, height;            /* along u and w, lattice units */
+    int32_t patches_u, patches_w;     /* patches_w = 1 in 2D */
+    int64_t grid_origin[2];           /* corner of the viewpoint grid (x, y) */
+    int64_t grid_step[2];
+    int32_t grid_nx, grid_ny;
+    int32_t n_layers;
+    const int64_t *layer_z;           /* [n_layers]; ignored in 2D */
+} vo_request;
+
+/* 0 on success, -1 on an invalid request. */
+int vo_check(const vo_scene *s, const vo_request *r);
+
+/* Patch centres, [patches_w * patches_u][3] units, index j = iw*patches_u + iu. */
+int vo_patch_centres(const vo_request *r, int64_t *out);
+
+/* Area (3D, m^2) or length (2D, m) of one patch. */
+double vo_patch_measure(const vo_request *r);
+
+/* Viewpoint centre of grid index ((layer*ny)+iy)*nx+ix, in units. */
+int vo_viewpoint(const vo_request *r, int64_t index, int64_t out[3]);
+
+/* 1 iff the closed segment q-p meets the closed box [lo, hi] (exact). */
+int vo_segment_hits_box(int dims, const int64_t q[3], const int64_t p[3],
+                        const int64_t lo[3], const int64_t hi[3]);
+
+/* Visibility of the target from viewpoint `index`.  If bits != NULL, the
+ * occlusion bit of every patch is written (ceil(P/32) words, bit j set iff
+ * patch j is blocked). */
+double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint32_t *bits);
+
+/* Visibility for n viewpoint indices on `threads` POSIX threads.
+ * bits_out (optional) holds n * ceil(P/32) words.  Returns 0 or -1. */
+int vo_run(const vo_scene *s, const vo_request *r, const int64_t *indices, int64_t n,
+           double *v_out, uint32_t *bits_out, int threads);
+
+/* Largest value of v[0..n). */
+double vo_max(const double *v, int64_t n);
+
+/* color = 0 if v == 0 else 1 + min(L-2, floor((L-1) * v / v_ref)). */
+int vo_quantise(const double *v, int64_t n, double v_ref, int levels, uint8_t *color_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
