@@ -1,0 +1,249 @@
+/*
+ * vcm.h -- C ABI of libvcm, a GB300 (sm_103a) engine for visibility color maps.
+ *
+ * A visibility color map (VCM, Def. 1 of Section II-A of "Scalable
+ * Visibility Color Map Construction in Spatial Databases") gives every point
+ * of a discretised space a color in [0,1] that grows with how much of a
+ * target T is visible from that point.  Visibility is the target's perceived
+ * size: the visual angle (Eq. 1, Section II-B.1), shrunk by oblique viewing
+ * (Section II-B.1, "Angle") and by obstacles that cut the line of sight
+ * (point-to-point visibility, Def. 2 of Section II-B.2).
+ *
+ * This library computes the target-centric VCM on a dense viewpoint grid:
+ *   - the target is an axis-aligned rectangle (3D) or segment (2D) split into
+ *     patches_u x patches_w equal patches represented by their centres (each
+ *     cell is represented by its centre, end of Section III-A);
+ *   - viewpoints are the centres of the cells of an nx x ny grid on each of
+ *     n_layers heights;
+ *   - the segment from viewpoint q to patch centre p is blocked iff it meets
+ *     an obstacle box; touching a box counts as meeting it (the shadow of an
+ *     obstacle contains the points whose segment to T "intersects or
+ *     touches" it, Def. 4 of Section III-B);
+ *   - v(q) = sum over unblocked patches with cos(theta) > 0 of
+ *     A cos(theta) / d^2 in 3D (solid angle of the visible part) or
+ *     len cos(theta) / d in 2D (visible subtended angle; for an unobstructed
+ *     target seen head-on this is Eq. 1);
+ *   - color = 0 if v == 0, else 1 + min(L-2, floor((L-1) v / v_ref)), with
+ *     v_ref the largest v of the request unless the caller gives one; level 0
+ *     is the color of obstructed points (Section III-C).
+ *
+ * COORDINATES.  All lengths are metres, float32, and must lie on the lattice
+ * of 2^-10 m with magnitude <= 16384 m (VCM_COORD_LIMIT_M); derived patch
+ * centres and viewpoints are rounded to that lattice (halves away from zero).
+ * Off-lattice, NaN or infinite inputs are rejected with VCM_E_ARG.  On this
+ * lattice the occlusion bits are exact: they equal the real-number answer.
+ *
+ * CONVENTIONS.  Every call returns a vcm_status and never throws or aborts.
+ * Host inputs are copied before the call returns; the caller keeps them.
+ * Buffers returned in vcm_result belong to the context until
+ * vcm_result_release.  Viewpoint order in outputs is ((layer*ny)+iy)*nx+ix.
+ * Occlusion bits (VCM_EMIT_BITS) are ceil(P/32) uint32 words per viewpoint,
+ * bit j of the viewpoint's bit string set iff patch j = iw*patches_u + iu is
+ * blocked.  vcm_last_error returns a message for the calling thread's last
+ * failed call.  A context may be used from several threads; calls that
+ * change the scene (load, build) must not overlap running requests.
+ */
+#ifndef VCM_H
+#define VCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vcm_ctx vcm_ctx;
+
+typedef enum {
+    VCM_OK = 0,
+    VCM_PENDING = 1,       /* vcm_poll: not finished yet */
+    VCM_E_ARG = -1,        /* invalid argument, off-lattice or non-finite input */
+    VCM_E_IO = -2,         /* scene file missing or malformed */
+    VCM_E_NOMEM = -3,      /* device memory or the context's budget exhausted */
+    VCM_E_CUDA = -4,       /* CUDA runtime error (message in vcm_last_error) */
+    VCM_E_TIMEOUT = -5,    /* vcm_poll wait elapsed, or a device-side bounded wait gave up */
+    VCM_E_CANCELLED = -6,  /* request cancelled before it ran */
+    VCM_E_STATE = -7       /* call out of order (e.g. submit before build) */
+} vcm_status;
+
+/* Axis codes for target orientation. */
+enum { VCM_AXIS_PX = 0, VCM_AXIS_NX = 1, VCM_AXIS_PY = 2, VCM_AXIS_NY = 3,
+       VCM_AXIS_PZ = 4, VCM_AXIS_NZ = 5 };
+
+/* Request flags. */
+enum { VCM_EMIT_BITS = 1u };   /* also produce the per-patch occlusion bits */
+
+#define VCM_UNITS_PER_M 1024
+#define VCM_COORD_LIMIT_M 16384.0f
+#define VCM_MAX_PATCHES_SIDE 4096u
+#define VCM_MAX_PATCHES 65536u
+#define VCM_MAX_LAYERS 4096u
+#define VCM_MAX_GRID_SIDE 65536u
+
+/* One VCM query (Def. 1: target-centric VCM of target T over a grid).
+ * 3D: T is the rectangle centred at `center`, spanning `width` along axis_u
+ * and `height` along axis_w, facing `normal` (three distinct axes).
+ * 2D: T is the segment centred at (center[0], center[1]) spanning `width`
+ * along axis_u (x or y), facing `normal` (the other of x, y); height,
+ * axis_w, patches_w, n_layers and layer_z are ignored.
+ * Patch (iu, iw) has centre center + ((iu+1/2)/patches_u - 1/2) width e_u
+ * + ((iw+1/2)/patches_w - 1/2) height e_w, e_u and e_w the signed unit
+ * vectors of axis_u and axis_w.
+ * Viewpoint (ix, iy, layer) is (grid_origin + (i+1/2) grid_step, layer_z[layer]). */
+typedef struct {
+    int32_t dims;            /* 2 or 3 */
+    float center[3];
+    int32_t axis_u, axis_w, normal;
+    float width, height;
+    uint32_t patches_u, patches_w;
+    float grid_origin[2], grid_step[2];
+    uint32_t grid_nx, grid_ny;
+    uint32_t n_layers;
+    const float *layer_z;    /* host pointer, n_layers heights; copied */
+    uint32_t color_levels;   /* L, 2..256 */
+    float v_ref;             /* > 0: normalise by this; <= 0: by the largest v */
+    uint32_t flags;          /* VCM_EMIT_BITS */
+} vcm_request;
+
+/* Per-request counters written by the device. */
+typedef struct {
+    float v_ref;                       /* the v_ref used for colors */
+    uint32_t vmax_bits;                /* largest v (float bits), accumulated on device */
+    uint32_t edge_cells;               /* viewpoints within 1e-5 (relative) of a color bin edge */
+    uint32_t error;                    /* nonzero: a device-side check failed (see vcm_last_error) */
+    unsigned long long slab_tests;     /* lane-level slab tests executed */
+    unsigned long long rechecked;      /* segments re-decided by the exact float64 predicate */
+    unsigned long long segments;       /* viewpoint-patch pairs decided (= viewpoints x patches) */
+    unsigned long long boxes_listed;   /* sum over tiles of culled candidate-list lengths */
+} vcm_stats;
+
+/* Results of a submitted request; all pointers owned by the context. */
+typedef struct {
+    const float *v;            /* host: visibility per viewpoint */
+    const uint8_t *color;      /* host: color level per viewpoint */
+    const uint32_t *bits;      /* host: occlusion bits (VCM_EMIT_BITS) or NULL */
+    const float *d_v;          /* device copies of the same */
+    const uint8_t *d_color;
+    const uint32_t *d_bits;
+    uint64_t n_viewpoints;
+    uint32_t words_per_viewpoint;
+    vcm_stats stats;
+    double latency_ms;         /* submit -> completion observed by the context */
+} vcm_result;
+
+/* Autotuned launch shape for one class of request (see vcm_autotune). */
+typedef struct {
+    uint32_t tile_x, tile_y;   /* viewpoints per tile (a tile is one block's work item) */
+    uint32_t patch_k;          /* patches per lane held in registers per pass (1..16) */
+    uint32_t box_cap;          /* candidate boxes staged in shared memory per tile */
+} vcm_tune;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes bounds the
+ * device memory that admitted requests may hold at once (0 = 64 GiB).
+ * The context owns the device scene, its index, streams and scratch. */
+vcm_status vcm_ctx_create(int device, size_t mem_budget_bytes, vcm_ctx **out);
+
+/* Wait for all work of the context, then free everything it owns. */
+void vcm_ctx_destroy(vcm_ctx *ctx);
+
+/* Message for the calling thread's last failed call ("" if none).  Valid
+ * until the next call on the same thread. */
+const char *vcm_last_error(vcm_ctx *ctx);
+
+/* ---- scene ------------------------------------------------------------ */
+
+/* Obstacles (the set O of Def. 1) as axis-aligned boxes, given by corners.
+ * lo/hi: host arrays of n_boxes x dims floats (dims = 2: rectangles in the
+ * plane; 3: boxes), lo <= hi componentwise, on the lattice.  Replaces any
+ * previous scene; the index must then be rebuilt with vcm_build. */
+vcm_status vcm_scene_load_mem(vcm_ctx *ctx, const float *lo, const float *hi,
+                              uint32_t n_boxes, int32_t dims);
+
+/* Same, from a file: "VCMS" magic, uint32 version = 1, int32 dims, uint32 n,
+ * then n*dims float32 lo and n*dims float32 hi (little endian). */
+vcm_status vcm_scene_load(vcm_ctx *ctx, const char *path);
+
+/* Write the current scene in the format read by vcm_scene_load. */
+vcm_status vcm_scene_save(vcm_ctx *ctx, const char *path);
+
+/* Build the device uniform-grid index over the box footprints (cell edge
+ * grid_cell_m metres, > 0; 0 picks one from the scene's density).  Boxes
+ * are bucketed by centre and each bucket keeps the bounds of its boxes.
+ * The scene is immutable afterwards until the next load.  Synchronous. */
+vcm_status vcm_build(vcm_ctx *ctx, float grid_cell_m);
+
+/* ---- direct device path ---------------------------------------------- */
+
+/* Enqueue one request on `stream` (a cudaStream_t; NULL = legacy default)
+ * writing into caller-owned device buffers: d_v (n_viewpoints floats),
+ * d_color (n_viewpoints bytes, or NULL to skip colors), d_bits
+ * (n_viewpoints * ceil(P/32) words, required iff VCM_EMIT_BITS) and d_stats
+ * (one vcm_stats).  Returns once the work is enqueued.  Calls on one
+ * context share its scratch and must not overlap on the device; issue them
+ * on one stream.  The first call for a larger shape may allocate scratch
+ * (and synchronises the device once). */
+vcm_status vcm_compute(vcm_ctx *ctx, const vcm_request *req, float *d_v, uint8_t *d_color,
+                       uint32_t *d_bits, vcm_stats *d_stats, void *stream);
+
+/* ---- asynchronous requests (continuous batching) --------------------- */
+
+/* Queue a request.  Non-blocking: a scheduler thread admits queued requests
+ * as execution slots and budgeted memory free up, and runs each admitted
+ * group as one persistent batched launch while other groups are still on
+ * the device.  VCM_E_NOMEM if the request alone exceeds the budget. */
+vcm_status vcm_submit(vcm_ctx *ctx, const vcm_request *req, uint64_t *ticket);
+
+/* Queue several requests that must run together in one batched launch. */
+vcm_status vcm_submit_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, uint64_t *tickets);
+
+/* VCM_OK when finished, VCM_PENDING if still queued or running after
+ * waiting up to wait_ms (-1 = forever), or the request's error. */
+vcm_status vcm_poll(vcm_ctx *ctx, uint64_t ticket, int32_t wait_ms);
+
+/* Results of a finished request (host copies and device buffers). */
+vcm_status vcm_result_get(vcm_ctx *ctx, uint64_t ticket, vcm_result *out);
+
+/* Free a finished or cancelled request's buffers and forget the ticket. */
+vcm_status vcm_result_release(vcm_ctx *ctx, uint64_t ticket);
+
+/* Cancel a request that has not been admitted yet (VCM_E_STATE if it has). */
+vcm_status vcm_cancel(vcm_ctx *ctx, uint64_t ticket);
+
+/* Scheduler limits: number of execution slots (streams; 1..16) and the
+ * largest number of requests merged into one launch. */
+vcm_status vcm_set_slots(vcm_ctx *ctx, uint32_t slots, uint32_t max_batch);
+
+/* ---- batching and tuning --------------------------------------------- */
+
+/* Run n requests as one persistent launch on `stream`, into caller-owned
+ * device buffers (arrays of n pointers, same meaning as vcm_compute). */
+vcm_status vcm_compute_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, float *const *d_v,
+                             uint8_t *const *d_color, uint32_t *const *d_bits, vcm_stats *d_stats,
+                             void *stream);
+
+/* Time candidate launch shapes on the given sample requests and keep the
+ * fastest per request class (patch count bucket); later launches use it.
+ * Writes the chosen shape for each sample to out (may be NULL). */
+vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vcm_tune *out);
+
+/* Force a launch shape for all later launches (tile_x = 0 restores tuning). */
+vcm_status vcm_set_tune(vcm_ctx *ctx, const vcm_tune *tune);
+
+/* Launch shape the context would use for this request. */
+vcm_status vcm_get_tune(vcm_ctx *ctx, const vcm_request *req, vcm_tune *out);
+
+/* ---- profiling --------------------------------------------------------- */
+
+/* Record two caller-created CUDA events (cudaEvent_t) on the launch stream
+ * immediately before and after the tile kernel of every later direct-path
+ * launch (vcm_compute, vcm_compute_batch); NULL, NULL stops.  The events
+ * must outlive their use. */
+vcm_status vcm_set_timing_events(vcm_ctx *ctx, void *before_tiles, void *after_tiles);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VCM_H */

@@ -1,0 +1,11 @@
+"""GB300-native visibility color maps (target-centric VCM, Def. 1 of
+"Scalable Visibility Color Map Construction in Spatial Databases").
+
+The compute path is libvcm.so (hand-written sm_103a CUDA behind the C ABI in
+include/vcm.h); ``vcm`` is its thin ctypes binding.  Build it with
+``paper_1310_7297_gb300.build.build()``.
+"""
+
+from .vcm import (  # noqa: F401
+    VCM_EMIT_BITS, Context, VcmError, lib, make_request, n_viewpoints, stats_from_tensor, words,
+)

@@ -1,0 +1,1577 @@
+// vcm_api.cpp -- host runtime behind the C ABI of include/vcm.h.
+//
+// Canonicalises requests onto the 2^-10 m lattice (exact integer rounding of
+// patch centres and viewpoints), owns the device scene and its grid index,
+// lays out launch descriptors, runs single requests on the caller's stream,
+// batches uneven requests into one persistent launch (replayed from a CUDA
+// graph), and schedules asynchronous requests onto execution slots with
+// memory-budget admission (continuous batching).
+#include "vcm_internal.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+using namespace vcm;
+
+namespace {
+
+thread_local std::string t_err;
+
+vcm_status fail(vcm_status s, const char *fmt, ...)
+{
+    char buf[768];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(e_ == cudaErrorMemoryAllocation ? VCM_E_NOMEM : VCM_E_CUDA,             \
+                        "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,       \
+                        __LINE__);                                                              \
+    } while (0)
+
+constexpr int64_t kLimitUnits = int64_t(1) << 24;
+constexpr double kUnitsPerM = 1024.0;
+
+bool to_units(float x, int64_t &u)
+{
+    if (!std::isfinite(x))
+        return false;
+    const double d = (double)x * kUnitsPerM;   // exact for a float
+    if (d != std::floor(d) || std::fabs(d) > (double)kLimitUnits)
+        return false;
+    u = (int64_t)d;
+    return true;
+}
+
+// nearest integer to num / den (den > 0), halves away from zero
+int64_t round_half_away(int64_t num, int64_t den)
+{
+    if (num >= 0)
+        return (2 * num + den) / (2 * den);
+    return -((2 * (-num) + den) / (2 * den));
+}
+
+float units_to_float(int64_t u) { return (float)((double)u / kUnitsPerM); }
+
+int pow2_at_least(int x)
+{
+    int p = 1;
+    while (p < x)
+        p <<= 1;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// canonical request
+// ---------------------------------------------------------------------------
+
+struct Canon {
+    int dims = 3;
+    int au = 0, an = 1, aw = 2, perm = 0;
+    float sn = 1.f, p_n = 0.f;
+    int nu = 1, nw = 1, P = 1, words = 1;
+    float measure = 0.f;
+    int nx = 1, ny = 1, nl = 1;
+    std::vector<float> u_coord, w_coord, x_coord, y_coord, z_coord;
+    float u_min = 0, u_max = 0, w_min = 0, w_max = 0;
+    int levels = 16;
+    float v_ref = 0.f;
+    unsigned flags = 0;
+    long long n_vp = 0;
+    size_t out_bytes() const
+    {
+        size_t b = (size_t)n_vp * (sizeof(float) + 1);
+        if (flags & VCM_EMIT_BITS)
+            b += (size_t)n_vp * words * sizeof(uint32_t);
+        return b;
+    }
+    int coord_count() const { return nu + nw + nx + ny + nl; }
+};
+
+int perm_index(int a0, int a1, int a2)
+{
+    static const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (int i = 0; i < 6; ++i)
+        if (P[i][0] == a0 && P[i][1] == a1 && P[i][2] == a2)
+            return i;
+    return -1;
+}
+
+vcm_status canonicalise(const vcm_request *r, Canon &c)
+{
+    if (!r)
+        return fail(VCM_E_ARG, "request is NULL");
+    if (r->dims != 2 && r->dims != 3)
+        return fail(VCM_E_ARG, "dims must be 2 or 3 (got %d)", r->dims);
+    c.dims = r->dims;
+    if (r->axis_u < 0 || r->axis_u > 5 || r->normal < 0 || r->normal > 5)
+        return fail(VCM_E_ARG, "axis codes must be 0..5");
+    if (r->flags & ~(uint32_t)VCM_EMIT_BITS)
+        return fail(VCM_E_ARG, "unknown flag bits 0x%x", r->flags);
+    c.flags = r->flags;
+    c.au = r->axis_u >> 1;
+    c.an = r->normal >> 1;
+    c.sn = (r->normal & 1) ? -1.f : 1.f;
+    const int64_t su = (r->axis_u & 1) ? -1 : 1;
+    int64_t sw = 1;
+    if (c.dims == 3) {
+        if (r->axis_w < 0 || r->axis_w > 5)
+            return fail(VCM_E_ARG, "axis_w must be 0..5");
+        c.aw = r->axis_w >> 1;
+        sw = (r->axis_w & 1) ? -1 : 1;
+        if (c.au == c.an || c.au == c.aw || c.an == c.aw)
+            return fail(VCM_E_ARG, "axis_u, axis_w and normal must be three different axes");
+    } else {
+        c.aw = 2;
+        if (c.au > 1 || c.an > 1 || c.au == c.an)
+            return fail(VCM_E_ARG, "2D target: axis_u and normal must be x and y in some order");
+    }
+    c.perm = perm_index(c.au, c.an, c.aw);
+    if (r->patches_u < 1 || r->patches_u > VCM_MAX_PATCHES_SIDE)
+        return fail(VCM_E_ARG, "patches_u must be 1..%u", VCM_MAX_PATCHES_SIDE);
+    c.nu = (int)r->patches_u;
+    c.nw = 1;
+    if (c.dims == 3) {
+        if (r->patches_w < 1 || r->patches_w > VCM_MAX_PATCHES_SIDE)
+            return fail(VCM_E_ARG, "patches_w must be 1..%u", VCM_MAX_PATCHES_SIDE);
+        c.nw = (int)r->patches_w;
+    }
+    c.P = c.nu * c.nw;
+    if ((unsigned)c.P > VCM_MAX_PATCHES)
+        return fail(VCM_E_ARG, "at most %u patches", VCM_MAX_PATCHES);
+    c.words = (c.P + 31) / 32;
+    int64_t cu[3];
+    for (int k = 0; k < 3; ++k) {
+        if (c.dims == 2 && k == 2) {
+            cu[k] = 0;
+            continue;
+        }
+        if (!to_units(r->center[k], cu[k]))
+            return fail(VCM_E_ARG, "center[%d] = %g is not a finite lattice value within 16384 m", k,
+                        (double)r->center[k]);
+    }
+    int64_t W = 0, H = 0;
+    if (!to_units(r->width, W) || W <= 0)
+        return fail(VCM_E_ARG, "width must be a positive lattice value");
+    if (c.dims == 3 && (!to_units(r->height, H) || H <= 0))
+        return fail(VCM_E_ARG, "height must be a positive lattice value");
+    // patch centres along u and w
+    c.u_coord.resize(c.nu);
+    for (int iu = 0; iu < c.nu; ++iu) {
+        const int64_t Nu = c.nu;
+        const int64_t v = round_half_away(2 * Nu * cu[c.au] + su * (2 * iu + 1 - Nu) * W, 2 * Nu);
+        if (v < -kLimitUnits || v > kLimitUnits)
+            return fail(VCM_E_ARG, "patch centre outside the coordinate limit");
+        c.u_coord[iu] = units_to_float(v);
+    }
+    c.w_coord.assign(c.nw, 0.f);
+    if (c.dims == 3) {
+        for (int iw = 0; iw < c.nw; ++iw) {
+            const int64_t Nw = c.nw;
+            const int64_t v = round_half_away(2 * Nw * cu[c.aw] + sw * (2 * iw + 1 - Nw) * H, 2 * Nw);
+            if (v < -kLimitUnits || v > kLimitUnits)
+                return fail(VCM_E_ARG, "patch centre outside the coordinate limit");
+            c.w_coord[iw] = units_to_float(v);
+        }
+    }
+    c.p_n = units_to_float(cu[c.an]);
+    c.u_min = *std::min_element(c.u_coord.begin(), c.u_coord.end());
+    c.u_max = *std::max_element(c.u_coord.begin(), c.u_coord.end());
+    c.w_min = *std::min_element(c.w_coord.begin(), c.w_coord.end());
+    c.w_max = *std::max_element(c.w_coord.begin(), c.w_coord.end());
+    {
+        const double lu = (double)W / kUnitsPerM / c.nu;
+        c.measure = (float)(c.dims == 3 ? lu * ((double)H / kUnitsPerM / c.nw) : lu);
+    }
+    // viewpoint grid
+    if (r->grid_nx < 1 || r->grid_ny < 1 || r->grid_nx > VCM_MAX_GRID_SIDE || r->grid_ny > VCM_MAX_GRID_SIDE)
+        return fail(VCM_E_ARG, "grid_nx and grid_ny must be 1..%u", VCM_MAX_GRID_SIDE);
+    c.nx = (int)r->grid_nx;
+    c.ny = (int)r->grid_ny;
+    int64_t o[2], s[2];
+    for (int k = 0; k < 2; ++k) {
+        if (!to_units(r->grid_origin[k], o[k]))
+            return fail(VCM_E_ARG, "grid_origin[%d] is not a finite lattice value", k);
+        if (!to_units(r->grid_step[k], s[k]) || s[k] <= 0)
+            return fail(VCM_E_ARG, "grid_step[%d] must be a positive lattice value", k);
+    }
+    c.x_coord.resize(c.nx);
+    c.y_coord.resize(c.ny);
+    for (int i = 0; i < c.nx; ++i) {
+        const int64_t v = round_half_away(2 * o[0] + (int64_t)(2 * i + 1) * s[0], 2);
+        if (v < -kLimitUnits || v > kLimitUnits)
+            return fail(VCM_E_ARG, "viewpoint x outside the coordinate limit");
+        c.x_coord[i] = units_to_float(v);
+    }
+    for (int i = 0; i < c.ny; ++i) {
+        const int64_t v = round_half_away(2 * o[1] + (int64_t)(2 * i + 1) * s[1], 2);
+        if (v < -kLimitUnits || v > kLimitUnits)
+            return fail(VCM_E_ARG, "viewpoint y outside the coordinate limit");
+        c.y_coord[i] = units_to_float(v);
+    }
+    if (c.dims == 3) {
+        if (r->n_layers < 1 || r->n_layers > VCM_MAX_LAYERS || !r->layer_z)
+            return fail(VCM_E_ARG, "n_layers must be 1..%u with layer_z given", VCM_MAX_LAYERS);
+        c.nl = (int)r->n_layers;
+        c.z_coord.resize(c.nl);
+        for (int l = 0; l < c.nl; ++l) {
+            int64_t z;
+            if (!to_units(r->layer_z[l], z))
+                return fail(VCM_E_ARG, "layer_z[%d] is not a finite lattice value", l);
+            c.z_coord[l] = units_to_float(z);
+        }
+    } else {
+        c.nl = 1;
+        c.z_coord.assign(1, 0.f);
+    }
+    if (r->color_levels < 2 || r->color_levels > 256)
+        return fail(VCM_E_ARG, "color_levels must be 2..256");
+    c.levels = (int)r->color_levels;
+    if (!std::isfinite(r->v_ref))
+        return fail(VCM_E_ARG, "v_ref must be finite");
+    c.v_ref = r->v_ref;
+    c.n_vp = (long long)c.nx * c.ny * c.nl;
+    return VCM_OK;
+}
+
+// lane mapping and tiling of a canonical request under a launch shape
+void fill_shape(const Canon &c, const vcm_tune &t, DevRequest &d)
+{
+    d.nuc = std::min(c.nu, 32);
+    d.groups = 32 / d.nuc;
+    d.col_passes = (c.nu + d.nuc - 1) / d.nuc;
+    const int rows_per_lane = (c.nw + d.groups - 1) / d.groups;
+    int k = pow2_at_least(std::min(rows_per_lane, 16));
+    if (t.patch_k > 0)
+        k = std::min(k, pow2_at_least(std::min<int>(t.patch_k, 16)));
+    d.k_rows = k;
+    d.row_passes = (c.nw + d.groups * k - 1) / (d.groups * k);
+    d.tile_x = (int)std::max(1u, t.tile_x);
+    d.tile_y = (int)std::max(1u, t.tile_y);
+    d.tiles_x = (c.nx + d.tile_x - 1) / d.tile_x;
+    d.tiles_y = (c.ny + d.tile_y - 1) / d.tile_y;
+    d.n_tiles = d.tiles_x * d.tiles_y * c.nl;
+}
+
+int tune_class(int P)
+{
+    if (P <= 32)
+        return 0;
+    if (P <= 128)
+        return 1;
+    if (P <= 512)
+        return 2;
+    if (P <= 2048)
+        return 3;
+    return 4;
+}
+constexpr int kTuneClasses = 5;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------
+// pinned host pool
+// ---------------------------------------------------------------------------
+
+class PinnedPool {
+  public:
+    ~PinnedPool()
+    {
+        for (auto &kv : free_)
+            cudaFreeHost(kv.second);
+    }
+    void *get(size_t bytes)
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        size_t want = std::max<size_t>(4096, (size_t)1 << (64 - __builtin_clzll(std::max<size_t>(bytes, 1) - 1 | 1)));
+        auto it = free_.lower_bound(want);
+        if (it != free_.end() && it->first <= 2 * want) {
+            void *p = it->second;
+            size_[p] = it->first;
+            free_.erase(it);
+            return p;
+        }
+        void *p = nullptr;
+        if (cudaMallocHost(&p, want) != cudaSuccess)
+            return nullptr;
+        size_[p] = want;
+        return p;
+    }
+    void put(void *p)
+    {
+        if (!p)
+            return;
+        std::lock_guard<std::mutex> g(mu_);
+        auto it = size_.find(p);
+        if (it == size_.end())
+            return;
+        free_.emplace(it->second, p);
+        size_.erase(it);
+    }
+
+  private:
+    std::mutex mu_;
+    std::multimap<size_t, void *> free_;
+    std::map<void *, size_t> size_;
+};
+
+// ---------------------------------------------------------------------------
+// launch resources
+// ---------------------------------------------------------------------------
+
+// Descriptor arena of one launch: DevRequest[n] | tile prefix | viewpoint
+// prefix | coordinates.  Built in pinned host memory, copied in one H2D.
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t desc_copied = nullptr;
+    char *d_desc = nullptr, *h_desc = nullptr;
+    size_t desc_cap = 0;
+    int *d_work = nullptr;
+    int *d_spill = nullptr;
+    size_t spill_cap = 0;   // ints
+    vcm_stats *d_stats = nullptr;
+    size_t stats_cap = 0;   // entries
+    bool busy = false;
+    // graph of the device work of one batched launch
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t graph_desc_bytes = 0;
+};
+
+struct Layout {
+    size_t off_reqs, off_tiles, off_vps, off_coords, bytes;
+    int total_tiles;
+    long long total_vp;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+struct Ticket;
+
+struct vcm_ctx {
+    int device = 0;
+    int sm_count = 1;
+    size_t budget = 0, used = 0;
+    std::mutex mu;             // guards everything below except the scene during launches
+    std::condition_variable cv;
+    // scene
+    int dims = 0;
+    uint32_t n_boxes = 0;
+    std::vector<float> h_lo, h_hi;   // n x 3
+    float *d_lo = nullptr, *d_hi = nullptr;
+    bool built = false;
+    float4 *d_perm[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int *d_cell_start = nullptr, *d_cell_of = nullptr, *d_count = nullptr, *d_cursor = nullptr, *d_order = nullptr;
+    float4 *d_cell_lo = nullptr, *d_cell_hi = nullptr;
+    unsigned *d_overhang = nullptr;
+    DevScene scene{};
+    // tuning
+    vcm_tune tune[kTuneClasses];
+    bool forced = false;
+    vcm_tune forced_tune{};
+    // launch slots
+    Slot direct;                      // vcm_compute / vcm_compute_batch
+    std::vector<std::unique_ptr<Slot>> slots;   // scheduler
+    uint32_t max_batch = 64;
+    cudaEvent_t ev_before = nullptr, ev_after = nullptr;   // optional timing of the tile kernel
+    PinnedPool pinned;
+    cudaStream_t aux = nullptr;
+    // scheduler
+    std::deque<std::vector<std::shared_ptr<Ticket>>> queue;
+    std::map<uint64_t, std::shared_ptr<Ticket>> tickets;
+    uint64_t next_ticket = 1;
+    std::thread worker;
+    bool stop = false;
+    int running_groups = 0;
+};
+
+namespace {
+
+enum TicketState { T_QUEUED, T_RUNNING, T_DONE, T_ERROR, T_CANCELLED };
+
+}  // namespace
+
+struct Ticket {
+    uint64_t id = 0;
+    Canon canon;
+    vcm_tune shape{};
+    TicketState state = T_QUEUED;
+    vcm_status err = VCM_OK;
+    std::string msg;
+    float *d_v = nullptr;
+    uint8_t *d_color = nullptr;
+    uint32_t *d_bits = nullptr;
+    float *h_v = nullptr;
+    uint8_t *h_color = nullptr;
+    uint32_t *h_bits = nullptr;
+    vcm_stats *h_stats = nullptr;
+    size_t bytes = 0;
+    Slot *slot = nullptr;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+namespace {
+
+vcm_tune default_tune()
+{
+    vcm_tune t;
+    t.tile_x = 8;
+    t.tile_y = 8;
+    t.patch_k = 0;
+    t.box_cap = 1024;
+    return t;
+}
+
+vcm_tune shape_for(vcm_ctx *ctx, const Canon &c)
+{
+    if (ctx->forced)
+        return ctx->forced_tune;
+    return ctx->tune[tune_class(c.P)];
+}
+
+Layout layout_for(const std::vector<const Canon *> &cs, const std::vector<vcm_tune> &shapes)
+{
+    Layout L{};
+    const size_t n = cs.size();
+    L.off_reqs = 0;
+    L.off_tiles = align_up(sizeof(DevRequest) * n, 256);
+    L.off_vps = align_up(L.off_tiles + sizeof(int) * (n + 1), 256);
+    L.off_coords = align_up(L.off_vps + sizeof(long long) * (n + 1), 256);
+    size_t coords = 0;
+    L.total_tiles = 0;
+    L.total_vp = 0;
+    for (size_t i = 0; i < n; ++i) {
+        coords += cs[i]->coord_count();
+        DevRequest d{};
+        fill_shape(*cs[i], shapes[i], d);
+        L.total_tiles += d.n_tiles;
+        L.total_vp += cs[i]->n_vp;
+    }
+    L.bytes = align_up(L.off_coords + sizeof(float) * coords, 256);
+    return L;
+}
+
+// Fill the pinned descriptor arena (host side) for a launch.
+void fill_desc(char *h, const char *d_base, const Layout &L, const std::vector<const Canon *> &cs,
+               const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
+               uint32_t *const *bits, vcm_stats *stats, int box_cap)
+{
+    const size_t n = cs.size();
+    DevRequest *reqs = reinterpret_cast<DevRequest *>(h + L.off_reqs);
+    int *tiles = reinterpret_cast<int *>(h + L.off_tiles);
+    long long *vps = reinterpret_cast<long long *>(h + L.off_vps);
+    float *coords = reinterpret_cast<float *>(h + L.off_coords);
+    const float *d_coords = reinterpret_cast<const float *>(d_base + L.off_coords);
+    size_t at = 0;
+    int tp = 0;
+    long long vp = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const Canon &c = *cs[i];
+        DevRequest d{};
+        d.dims = c.dims;
+        d.au = c.au; d.an = c.an; d.aw = c.aw; d.perm = c.perm;
+        d.sn = c.sn; d.p_n = c.p_n;
+        d.nu = c.nu; d.nw = c.nw; d.P = c.P; d.words = c.words;
+        d.measure = c.measure;
+        d.nx = c.nx; d.ny = c.ny; d.nl = c.nl;
+        fill_shape(c, shapes[i], d);
+        auto put = [&](const std::vector<float> &src) {
+            const float *dp = d_coords + at;
+            std::memcpy(coords + at, src.data(), sizeof(float) * src.size());
+            at += src.size();
+            return dp;
+        };
+        d.u_coord = put(c.u_coord);
+        d.w_coord = put(c.w_coord);
+        d.x_coord = put(c.x_coord);
+        d.y_coord = put(c.y_coord);
+        d.z_coord = put(c.z_coord);
+        d.u_min = c.u_min; d.u_max = c.u_max; d.w_min = c.w_min; d.w_max = c.w_max;
+        d.v_out = v[i];
+        d.color_out = color ? color[i] : nullptr;
+        d.bits_out = bits ? bits[i] : nullptr;
+        d.stats = stats + i;
+        d.v_ref_given = c.v_ref;
+        d.levels = c.levels;
+        d.flags = c.flags;
+        d.box_cap = box_cap;
+        reqs[i] = d;
+        tiles[i] = tp;
+        vps[i] = vp;
+        tp += d.n_tiles;
+        vp += c.n_vp;
+    }
+    tiles[n] = tp;
+    vps[n] = vp;
+}
+
+vcm_status ensure_slot(vcm_ctx *ctx, Slot &s, size_t desc_bytes, size_t n_stats, int grid_blocks,
+                       cudaStream_t sync_stream)
+{
+    const size_t spill_need = (size_t)grid_blocks * std::max<uint32_t>(ctx->n_boxes, 1);
+    const bool grow = desc_bytes > s.desc_cap || spill_need > s.spill_cap || n_stats > s.stats_cap ||
+                      !s.d_work;
+    if (!grow)
+        return VCM_OK;
+    // the slot's buffers may still be read by queued work
+    CUDA_TRY(cudaStreamSynchronize(sync_stream));
+    if (s.stream && s.stream != sync_stream)
+        CUDA_TRY(cudaStreamSynchronize(s.stream));
+    if (!s.desc_copied)
+        CUDA_TRY(cudaEventCreateWithFlags(&s.desc_copied, cudaEventDisableTiming));
+    if (!s.d_work)
+        CUDA_TRY(cudaMalloc(&s.d_work, 256));
+    if (desc_bytes > s.desc_cap) {
+        size_t cap = std::max<size_t>(desc_bytes * 2, 1 << 16);
+        if (s.d_desc) cudaFree(s.d_desc);
+        if (s.h_desc) cudaFreeHost(s.h_desc);
+        s.d_desc = nullptr;
+        s.h_desc = nullptr;
+        CUDA_TRY(cudaMalloc(&s.d_desc, cap));
+        CUDA_TRY(cudaMallocHost(&s.h_desc, cap));
+        s.desc_cap = cap;
+        if (s.exec) {
+            cudaGraphExecDestroy(s.exec);
+            s.exec = nullptr;
+        }
+        if (s.graph) {
+            cudaGraphDestroy(s.graph);
+            s.graph = nullptr;
+        }
+    }
+    if (spill_need > s.spill_cap) {
+        if (s.d_spill) cudaFree(s.d_spill);
+        s.d_spill = nullptr;
+        CUDA_TRY(cudaMalloc(&s.d_spill, spill_need * sizeof(int)));
+        s.spill_cap = spill_need;
+    }
+    if (n_stats > s.stats_cap) {
+        size_t cap = std::max<size_t>(n_stats, 256);
+        if (s.d_stats) cudaFree(s.d_stats);
+        s.d_stats = nullptr;
+        CUDA_TRY(cudaMalloc(&s.d_stats, cap * sizeof(vcm_stats)));
+        s.stats_cap = cap;
+    }
+    return VCM_OK;
+}
+
+int launch_box_cap(const std::vector<vcm_tune> &shapes)
+{
+    uint32_t cap = 256;
+    for (auto &t : shapes)
+        cap = std::max(cap, t.box_cap);
+    return (int)std::min<uint32_t>(cap, 5000);
+}
+
+int grid_blocks_for(vcm_ctx *ctx, int box_cap, int total_tiles)
+{
+    const int per_sm = tiles_blocks_per_sm(box_cap, 16);
+    return std::max(1, std::min(total_tiles, per_sm * ctx->sm_count));
+}
+
+struct Prepared {
+    Layout L;
+    int box_cap = 0;
+    int blocks = 0;
+    size_t n = 0;
+};
+
+// Host half of a launch: layout, scratch, and the descriptor arena filled in
+// pinned memory.  `stats` must hold cs.size() entries.
+vcm_status prepare_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *> &cs,
+                          const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
+                          uint32_t *const *bits, vcm_stats *stats, cudaStream_t sync_stream, Prepared &P)
+{
+    if (!ctx->built)
+        return fail(VCM_E_STATE, "vcm_build has not been called for the current scene");
+    P.L = layout_for(cs, shapes);
+    P.box_cap = launch_box_cap(shapes);
+    P.blocks = grid_blocks_for(ctx, P.box_cap, P.L.total_tiles);
+    P.n = cs.size();
+    vcm_status st = ensure_slot(ctx, s, P.L.bytes, cs.size(), P.blocks, sync_stream);
+    if (st != VCM_OK)
+        return st;
+    // the previous upload from h_desc must have completed before rewriting it
+    CUDA_TRY(cudaEventSynchronize(s.desc_copied));
+    fill_desc(s.h_desc, s.d_desc, P.L, cs, shapes, v, color, bits, stats, P.box_cap);
+    return VCM_OK;
+}
+
+// Device half: descriptor upload, counters, bit buffers, the persistent tile
+// kernel and the quantiser, in stream order.  The node sequence is the same
+// for every launch, so a captured graph can be updated in place.
+vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *stats, cudaStream_t stream,
+                         bool timed = false)
+{
+    CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, P.L.bytes, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaEventRecord(s.desc_copied, stream));
+    CUDA_TRY(cudaMemsetAsync(s.d_work, 0, sizeof(int), stream));
+    CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(vcm_stats) * P.n, stream));
+    const DevRequest *d_reqs = reinterpret_cast<const DevRequest *>(s.d_desc + P.L.off_reqs);
+    const int *d_tiles = reinterpret_cast<const int *>(s.d_desc + P.L.off_tiles);
+    const long long *d_vps = reinterpret_cast<const long long *>(s.d_desc + P.L.off_vps);
+    CUDA_TRY(launch_zero_bits(d_reqs, (int)P.n, stream));
+    if (timed && ctx->ev_before)
+        CUDA_TRY(cudaEventRecord(ctx->ev_before, stream));
+    CUDA_TRY(launch_tiles(ctx->scene, d_reqs, d_tiles, (int)P.n, P.L.total_tiles, s.d_work, s.d_spill,
+                          P.blocks, P.box_cap, 16, stream));
+    if (timed && ctx->ev_after)
+        CUDA_TRY(cudaEventRecord(ctx->ev_after, stream));
+    CUDA_TRY(launch_quantise(d_reqs, d_vps, (int)P.n, P.L.total_vp, stream));
+    return VCM_OK;
+}
+
+vcm_status enqueue_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *> &cs,
+                          const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
+                          uint32_t *const *bits, vcm_stats *stats, cudaStream_t stream, bool timed = false)
+{
+    Prepared P;
+    vcm_status st = prepare_launch(ctx, s, cs, shapes, v, color, bits, stats, stream, P);
+    if (st != VCM_OK)
+        return st;
+    return record_launch(ctx, s, P, stats, stream, timed);
+}
+
+// Same device work, captured into the slot's graph (updated in place when
+// the topology allows, re-instantiated otherwise) and launched.
+vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *> &cs,
+                         const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
+                         uint32_t *const *bits, vcm_stats *stats)
+{
+    Prepared P;
+    vcm_status st = prepare_launch(ctx, s, cs, shapes, v, color, bits, stats, s.stream, P);
+    if (st != VCM_OK)
+        return st;
+    CUDA_TRY(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeRelaxed));
+    st = record_launch(ctx, s, P, stats, s.stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s.stream, &g);
+    if (st != VCM_OK) {
+        if (g)
+            cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess)
+        return fail(VCM_E_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    if (s.exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(s.exec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(s.exec);
+            s.exec = nullptr;
+        }
+    }
+    if (!s.exec) {
+        e = cudaGraphInstantiate(&s.exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            s.exec = nullptr;
+            return fail(VCM_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    if (s.graph)
+        cudaGraphDestroy(s.graph);
+    s.graph = g;
+    CUDA_TRY(cudaGraphLaunch(s.exec, s.stream));
+    return VCM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// scene
+// ---------------------------------------------------------------------------
+
+void free_scene(vcm_ctx *ctx)
+{
+    cudaFree(ctx->d_lo);
+    cudaFree(ctx->d_hi);
+    ctx->d_lo = ctx->d_hi = nullptr;
+    for (auto &p : ctx->d_perm) {
+        cudaFree(p);
+        p = nullptr;
+    }
+    cudaFree(ctx->d_cell_start);
+    cudaFree(ctx->d_cell_of);
+    cudaFree(ctx->d_count);
+    cudaFree(ctx->d_cursor);
+    cudaFree(ctx->d_order);
+    cudaFree(ctx->d_cell_lo);
+    cudaFree(ctx->d_cell_hi);
+    cudaFree(ctx->d_overhang);
+    ctx->d_cell_start = ctx->d_cell_of = ctx->d_count = ctx->d_cursor = ctx->d_order = nullptr;
+    ctx->d_cell_lo = ctx->d_cell_hi = nullptr;
+    ctx->d_overhang = nullptr;
+    ctx->built = false;
+}
+
+bool scheduler_idle(vcm_ctx *ctx) { return ctx->queue.empty() && ctx->running_groups == 0; }
+
+// ---------------------------------------------------------------------------
+// scheduler
+// ---------------------------------------------------------------------------
+
+struct Done {
+    vcm_ctx *ctx;
+    std::vector<std::shared_ptr<Ticket>> group;
+    Slot *slot;
+};
+
+void CUDART_CB on_group_done(void *arg)
+{
+    Done *d = static_cast<Done *>(arg);
+    {
+        std::lock_guard<std::mutex> g(d->ctx->mu);
+        const auto now = std::chrono::steady_clock::now();
+        for (auto &t : d->group) {
+            if (t->h_stats && t->h_stats->error)
+                t->state = T_ERROR, t->err = VCM_E_CUDA, t->msg = "device-side check failed";
+            else
+                t->state = T_DONE;
+            t->t_done = now;
+        }
+        d->slot->busy = false;
+        d->ctx->running_groups--;
+    }
+    d->ctx->cv.notify_all();
+    delete d;
+}
+
+void release_buffers(vcm_ctx *ctx, Ticket &t)
+{
+    if (t.d_v)
+        cudaFreeAsync(t.d_v, ctx->aux);
+    t.d_v = nullptr;
+    t.d_color = nullptr;
+    t.d_bits = nullptr;
+    ctx->pinned.put(t.h_v);
+    t.h_v = nullptr;
+    t.h_color = nullptr;
+    t.h_bits = nullptr;
+    t.h_stats = nullptr;
+    if (t.bytes) {
+        ctx->used -= t.bytes;
+        t.bytes = 0;
+    }
+}
+
+// Allocate one request's device and pinned buffers (one block each).
+// Layout: v (floats) | color | bits | stats.
+bool alloc_buffers(vcm_ctx *ctx, Ticket &t, cudaStream_t stream)
+{
+    const Canon &c = t.canon;
+    const size_t n = (size_t)c.n_vp;
+    const size_t off_color = align_up(n * 4, 256);
+    const size_t off_bits = align_up(off_color + n, 256);
+    const size_t bits_bytes = (c.flags & VCM_EMIT_BITS) ? n * c.words * 4 : 0;
+    const size_t off_stats = align_up(off_bits + bits_bytes, 256);
+    const size_t total = off_stats + sizeof(vcm_stats);
+    char *d = nullptr;
+    if (cudaMallocAsync((void **)&d, total, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    char *h = static_cast<char *>(ctx->pinned.get(total));
+    if (!h) {
+        cudaFreeAsync(d, stream);
+        return false;
+    }
+    t.d_v = reinterpret_cast<float *>(d);
+    t.d_color = reinterpret_cast<uint8_t *>(d + off_color);
+    t.d_bits = bits_bytes ? reinterpret_cast<uint32_t *>(d + off_bits) : nullptr;
+    t.h_v = reinterpret_cast<float *>(h);
+    t.h_color = reinterpret_cast<uint8_t *>(h + off_color);
+    t.h_bits = bits_bytes ? reinterpret_cast<uint32_t *>(h + off_bits) : nullptr;
+    t.h_stats = reinterpret_cast<vcm_stats *>(h + off_stats);
+    return true;
+}
+
+// Launch one admitted group on its slot (called with ctx->mu held).
+void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &group)
+{
+    std::vector<const Canon *> cs;
+    std::vector<vcm_tune> shapes;
+    std::vector<float *> v;
+    std::vector<uint8_t *> col;
+    std::vector<uint32_t *> bits;
+    for (auto &t : group) {
+        cs.push_back(&t->canon);
+        shapes.push_back(t->shape);
+        v.push_back(t->d_v);
+        col.push_back(t->d_color);
+        bits.push_back(t->d_bits);
+    }
+    vcm_status st = ensure_slot(ctx, s, 0, group.size(), 1, s.stream);
+    if (st == VCM_OK)
+        st = enqueue_graph(ctx, s, cs, shapes, v.data(), col.data(), bits.data(), s.d_stats);
+    if (st == VCM_OK) {
+        for (size_t i = 0; i < group.size(); ++i) {
+            Ticket &t = *group[i];
+            const Canon &c = t.canon;
+            cudaMemcpyAsync(t.h_v, t.d_v, (size_t)c.n_vp * 4, cudaMemcpyDeviceToHost, s.stream);
+            cudaMemcpyAsync(t.h_color, t.d_color, (size_t)c.n_vp, cudaMemcpyDeviceToHost, s.stream);
+            if (t.d_bits)
+                cudaMemcpyAsync(t.h_bits, t.d_bits, (size_t)c.n_vp * c.words * 4, cudaMemcpyDeviceToHost,
+                                s.stream);
+            cudaMemcpyAsync(t.h_stats, s.d_stats + i, sizeof(vcm_stats), cudaMemcpyDeviceToHost, s.stream);
+        }
+        Done *d = new Done{ctx, group, &s};
+        if (cudaLaunchHostFunc(s.stream, on_group_done, d) == cudaSuccess) {
+            for (auto &t : group) {
+                t->state = T_RUNNING;
+                t->slot = &s;
+            }
+            s.busy = true;
+            ctx->running_groups++;
+            return;
+        }
+        delete d;
+        st = fail(VCM_E_CUDA, "cudaLaunchHostFunc failed");
+    }
+    for (auto &t : group) {
+        t->state = T_ERROR;
+        t->err = st;
+        t->msg = t_err;
+        t->t_done = std::chrono::steady_clock::now();
+        release_buffers(ctx, *t);
+    }
+}
+
+void scheduler_loop(vcm_ctx *ctx)
+{
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    while (!ctx->stop) {
+        Slot *free_slot = nullptr;
+        for (auto &s : ctx->slots)
+            if (!s->busy) {
+                free_slot = s.get();
+                break;
+            }
+        if (ctx->queue.empty() || !free_slot) {
+            ctx->cv.wait(lk);
+            continue;
+        }
+        // admit groups from the front of the queue while memory allows
+        std::vector<std::shared_ptr<Ticket>> batch;
+        while (!ctx->queue.empty()) {
+            auto &grp = ctx->queue.front();
+            size_t need = 0;
+            for (auto &t : grp)
+                need += t->canon.out_bytes() + 1024;
+            if (!batch.empty() && batch.size() + grp.size() > ctx->max_batch)
+                break;
+            if (ctx->used + need > ctx->budget)
+                break;
+            bool ok = true;
+            for (auto &t : grp) {
+                if (!alloc_buffers(ctx, *t, free_slot->stream)) {
+                    ok = false;
+                    break;
+                }
+                t->bytes = t->canon.out_bytes() + 1024;
+                ctx->used += t->bytes;
+            }
+            if (!ok) {
+                for (auto &t : grp)
+                    release_buffers(ctx, *t);
+                break;
+            }
+            for (auto &t : grp)
+                batch.push_back(t);
+            ctx->queue.pop_front();
+        }
+        if (batch.empty()) {
+            // the head does not fit while other work holds memory: wait
+            if (ctx->running_groups == 0) {
+                auto grp = ctx->queue.front();
+                ctx->queue.pop_front();
+                for (auto &t : grp) {
+                    t->state = T_ERROR;
+                    t->err = VCM_E_NOMEM;
+                    t->msg = "request does not fit in device memory";
+                    t->t_done = std::chrono::steady_clock::now();
+                }
+                ctx->cv.notify_all();
+            } else {
+                ctx->cv.wait(lk);
+            }
+            continue;
+        }
+        launch_group(ctx, *free_slot, batch);
+        ctx->cv.notify_all();
+    }
+}
+
+vcm_status start_scheduler(vcm_ctx *ctx, uint32_t n_slots)
+{
+    for (uint32_t i = 0; i < n_slots; ++i) {
+        auto s = std::make_unique<Slot>();
+        CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&s->desc_copied, cudaEventDisableTiming));
+        ctx->slots.push_back(std::move(s));
+    }
+    ctx->stop = false;
+    ctx->worker = std::thread(scheduler_loop, ctx);
+    return VCM_OK;
+}
+
+void stop_scheduler(vcm_ctx *ctx)
+{
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->stop = true;
+    }
+    ctx->cv.notify_all();
+    if (ctx->worker.joinable())
+        ctx->worker.join();
+    for (auto &s : ctx->slots) {
+        if (s->stream)
+            cudaStreamSynchronize(s->stream);
+    }
+}
+
+void destroy_slot(Slot &s)
+{
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.graph) cudaGraphDestroy(s.graph);
+    if (s.d_desc) cudaFree(s.d_desc);
+    if (s.h_desc) cudaFreeHost(s.h_desc);
+    if (s.d_work) cudaFree(s.d_work);
+    if (s.d_spill) cudaFree(s.d_spill);
+    if (s.d_stats) cudaFree(s.d_stats);
+    if (s.desc_copied) cudaEventDestroy(s.desc_copied);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    s = Slot{};
+}
+
+vcm_status validate_ctx(vcm_ctx *ctx)
+{
+    if (!ctx)
+        return fail(VCM_E_ARG, "context is NULL");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess)
+        return fail(VCM_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return VCM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+vcm_status vcm_ctx_create(int device, size_t mem_budget_bytes, vcm_ctx **out)
+{
+    try {
+        if (!out)
+            return fail(VCM_E_ARG, "out is NULL");
+        *out = nullptr;
+        int n = 0;
+        cudaError_t e = cudaGetDeviceCount(&n);
+        if (e != cudaSuccess || n == 0)
+            return fail(VCM_E_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+        if (device < 0 || device >= n)
+            return fail(VCM_E_ARG, "device %d out of range (%d devices)", device, n);
+        CUDA_TRY(cudaSetDevice(device));
+        CUDA_TRY(init_device());
+        auto ctx = std::make_unique<vcm_ctx>();
+        ctx->device = device;
+        CUDA_TRY(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
+        ctx->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)64 << 30;
+        for (auto &t : ctx->tune)
+            t = default_tune();
+        CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&ctx->direct.desc_copied, cudaEventDisableTiming));
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        vcm_status st = start_scheduler(ctx.get(), 4);
+        if (st != VCM_OK)
+            return st;
+        *out = ctx.release();
+        return VCM_OK;
+    } catch (const std::exception &ex) {
+        return fail(VCM_E_NOMEM, "vcm_ctx_create: %s", ex.what());
+    }
+}
+
+void vcm_ctx_destroy(vcm_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    cudaSetDevice(ctx->device);
+    stop_scheduler(ctx);
+    cudaDeviceSynchronize();
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        for (auto &kv : ctx->tickets)
+            release_buffers(ctx, *kv.second);
+        ctx->tickets.clear();
+    }
+    cudaStreamSynchronize(ctx->aux);
+    for (auto &s : ctx->slots)
+        destroy_slot(*s);
+    destroy_slot(ctx->direct);
+    free_scene(ctx);
+    if (ctx->aux)
+        cudaStreamDestroy(ctx->aux);
+    delete ctx;
+}
+
+const char *vcm_last_error(vcm_ctx *)
+{
+    return t_err.c_str();
+}
+
+vcm_status vcm_scene_load_mem(vcm_ctx *ctx, const float *lo, const float *hi, uint32_t n_boxes, int32_t dims)
+{
+    try {
+        vcm_status st = validate_ctx(ctx);
+        if (st != VCM_OK)
+            return st;
+        if (dims != 2 && dims != 3)
+            return fail(VCM_E_ARG, "dims must be 2 or 3");
+        if (n_boxes > 0 && (!lo || !hi))
+            return fail(VCM_E_ARG, "lo/hi are NULL");
+        if (n_boxes > (1u << 26))
+            return fail(VCM_E_ARG, "too many boxes (%u)", n_boxes);
+        std::vector<float> L((size_t)n_boxes * 3, 0.f), H((size_t)n_boxes * 3, 0.f);
+        for (uint32_t i = 0; i < n_boxes; ++i)
+            for (int k = 0; k < dims; ++k) {
+                const float a = lo[(size_t)i * dims + k], b = hi[(size_t)i * dims + k];
+                int64_t ua, ub;
+                if (!to_units(a, ua) || !to_units(b, ub))
+                    return fail(VCM_E_ARG, "box %u coordinate %d is not a finite lattice value within 16384 m", i, k);
+                if (ua > ub)
+                    return fail(VCM_E_ARG, "box %u has lo > hi on axis %d", i, k);
+                L[(size_t)i * 3 + k] = a;
+                H[(size_t)i * 3 + k] = b;
+            }
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (!scheduler_idle(ctx))
+            return fail(VCM_E_STATE, "requests are still queued or running");
+        CUDA_TRY(cudaDeviceSynchronize());
+        free_scene(ctx);
+        ctx->dims = dims;
+        ctx->n_boxes = n_boxes;
+        ctx->h_lo.swap(L);
+        ctx->h_hi.swap(H);
+        const size_t bytes = std::max<size_t>(1, (size_t)n_boxes * 3) * sizeof(float);
+        CUDA_TRY(cudaMalloc(&ctx->d_lo, bytes));
+        CUDA_TRY(cudaMalloc(&ctx->d_hi, bytes));
+        if (n_boxes) {
+            CUDA_TRY(cudaMemcpy(ctx->d_lo, ctx->h_lo.data(), (size_t)n_boxes * 12, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(ctx->d_hi, ctx->h_hi.data(), (size_t)n_boxes * 12, cudaMemcpyHostToDevice));
+        }
+        return VCM_OK;
+    } catch (const std::exception &ex) {
+        return fail(VCM_E_NOMEM, "vcm_scene_load_mem: %s", ex.what());
+    }
+}
+
+vcm_status vcm_scene_load(vcm_ctx *ctx, const char *path)
+{
+    if (!path)
+        return fail(VCM_E_ARG, "path is NULL");
+    FILE *f = fopen(path, "rb");
+    if (!f)
+        return fail(VCM_E_IO, "cannot open %s", path);
+    char magic[4];
+    uint32_t version = 0, n = 0;
+    int32_t dims = 0;
+    bool ok = fread(magic, 1, 4, f) == 4 && std::memcmp(magic, "VCMS", 4) == 0 &&
+              fread(&version, 4, 1, f) == 1 && version == 1 && fread(&dims, 4, 1, f) == 1 &&
+              fread(&n, 4, 1, f) == 1 && (dims == 2 || dims == 3) && n <= (1u << 26);
+    std::vector<float> lo, hi;
+    if (ok) {
+        lo.resize((size_t)n * dims);
+        hi.resize((size_t)n * dims);
+        ok = fread(lo.data(), sizeof(float), lo.size(), f) == lo.size() &&
+             fread(hi.data(), sizeof(float), hi.size(), f) == hi.size();
+        char extra;
+        if (ok && fread(&extra, 1, 1, f) == 1)
+            ok = false;   // trailing bytes
+    }
+    fclose(f);
+    if (!ok)
+        return fail(VCM_E_IO, "%s is not a valid scene file", path);
+    return vcm_scene_load_mem(ctx, lo.data(), hi.data(), n, dims);
+}
+
+vcm_status vcm_scene_save(vcm_ctx *ctx, const char *path)
+{
+    if (!ctx || !path)
+        return fail(VCM_E_ARG, "NULL argument");
+    if (ctx->dims == 0)
+        return fail(VCM_E_STATE, "no scene loaded");
+    FILE *f = fopen(path, "wb");
+    if (!f)
+        return fail(VCM_E_IO, "cannot write %s", path);
+    const uint32_t version = 1, n = ctx->n_boxes;
+    const int32_t dims = ctx->dims;
+    bool ok = fwrite("VCMS", 1, 4, f) == 4 && fwrite(&version, 4, 1, f) == 1 && fwrite(&dims, 4, 1, f) == 1 &&
+              fwrite(&n, 4, 1, f) == 1;
+    for (int pass = 0; pass < 2 && ok; ++pass) {
+        const std::vector<float> &src = pass ? ctx->h_hi : ctx->h_lo;
+        for (uint32_t i = 0; i < n && ok; ++i)
+            ok = fwrite(&src[(size_t)i * 3], sizeof(float), dims, f) == (size_t)dims;
+    }
+    ok = (fclose(f) == 0) && ok;
+    return ok ? VCM_OK : fail(VCM_E_IO, "write to %s failed", path);
+}
+
+vcm_status vcm_build(vcm_ctx *ctx, float grid_cell_m)
+{
+    try {
+        vcm_status st = validate_ctx(ctx);
+        if (st != VCM_OK)
+            return st;
+        if (ctx->dims == 0)
+            return fail(VCM_E_STATE, "no scene loaded");
+        if (!std::isfinite(grid_cell_m) || grid_cell_m < 0.f)
+            return fail(VCM_E_ARG, "grid_cell_m must be >= 0");
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (!scheduler_idle(ctx))
+            return fail(VCM_E_STATE, "requests are still queued or running");
+        const uint32_t n = ctx->n_boxes;
+        double x0 = 0, x1 = 1, y0 = 0, y1 = 1, side = 0;
+        if (n) {
+            x0 = y0 = 1e30;
+            x1 = y1 = -1e30;
+            for (uint32_t i = 0; i < n; ++i) {
+                x0 = std::min<double>(x0, ctx->h_lo[3 * i]);
+                y0 = std::min<double>(y0, ctx->h_lo[3 * i + 1]);
+                x1 = std::max<double>(x1, ctx->h_hi[3 * i]);
+                y1 = std::max<double>(y1, ctx->h_hi[3 * i + 1]);
+                side += std::sqrt(std::max(0.0, (double)(ctx->h_hi[3 * i] - ctx->h_lo[3 * i]) *
+                                                    (ctx->h_hi[3 * i + 1] - ctx->h_lo[3 * i + 1])));
+            }
+            side /= n;
+        }
+        const double w = std::max(x1 - x0, 1.0), h = std::max(y1 - y0, 1.0);
+        double cell = grid_cell_m;
+        if (cell <= 0.0)
+            cell = std::max({side, std::sqrt(w * h / std::max<uint32_t>(n, 1)) * 1.5, 1.0});
+        // keep the grid at most 4M cells
+        while ((w / cell + 1) * (h / cell + 1) > 4.0e6)
+            cell *= 1.5;
+        const int gnx = (int)std::ceil(w / cell) + 1, gny = (int)std::ceil(h / cell) + 1;
+        const int n_cells = gnx * gny;
+        for (auto &p : ctx->d_perm) {
+            cudaFree(p);
+            p = nullptr;
+        }
+        cudaFree(ctx->d_cell_start); cudaFree(ctx->d_cell_of); cudaFree(ctx->d_count);
+        cudaFree(ctx->d_cursor); cudaFree(ctx->d_order); cudaFree(ctx->d_cell_lo); cudaFree(ctx->d_cell_hi);
+        cudaFree(ctx->d_overhang);
+        const size_t nb = std::max<uint32_t>(n, 1);
+        for (auto &p : ctx->d_perm)
+            CUDA_TRY(cudaMalloc(&p, nb * 2 * sizeof(float4)));
+        CUDA_TRY(cudaMalloc(&ctx->d_cell_start, sizeof(int) * (n_cells + 1)));
+        CUDA_TRY(cudaMalloc(&ctx->d_cell_of, sizeof(int) * nb));
+        CUDA_TRY(cudaMalloc(&ctx->d_count, sizeof(int) * n_cells));
+        CUDA_TRY(cudaMalloc(&ctx->d_cursor, sizeof(int) * n_cells));
+        CUDA_TRY(cudaMalloc(&ctx->d_order, sizeof(int) * nb));
+        CUDA_TRY(cudaMalloc(&ctx->d_cell_lo, sizeof(float4) * n_cells));
+        CUDA_TRY(cudaMalloc(&ctx->d_cell_hi, sizeof(float4) * n_cells));
+        CUDA_TRY(cudaMalloc(&ctx->d_overhang, sizeof(unsigned)));
+        CUDA_TRY(launch_grid_build(ctx->d_lo, ctx->d_hi, (int)n, ctx->dims, (float)x0, (float)y0, (float)cell, gnx,
+                                   gny, ctx->d_cell_of, ctx->d_count, ctx->d_cursor, ctx->d_order,
+                                   ctx->d_cell_start, ctx->d_perm, ctx->d_cell_lo, ctx->d_cell_hi,
+                                   ctx->d_overhang, ctx->aux));
+        CUDA_TRY(cudaStreamSynchronize(ctx->aux));
+        unsigned oh_bits = 0;
+        CUDA_TRY(cudaMemcpy(&oh_bits, ctx->d_overhang, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        float oh;
+        std::memcpy(&oh, &oh_bits, 4);
+        DevScene &sc = ctx->scene;
+        for (int p = 0; p < 6; ++p)
+            sc.boxes[p] = ctx->d_perm[p];
+        sc.n_boxes = (int)n;
+        sc.dims = ctx->dims;
+        sc.cell_start = ctx->d_cell_start;
+        sc.cell_lo = ctx->d_cell_lo;
+        sc.cell_hi = ctx->d_cell_hi;
+        sc.gx0 = (float)x0;
+        sc.gy0 = (float)y0;
+        sc.cell = (float)cell;
+        sc.inv_cell = (float)(1.0 / cell);
+        sc.gnx = gnx;
+        sc.gny = gny;
+        sc.overhang = oh;
+        ctx->built = true;
+        return VCM_OK;
+    } catch (const std::exception &ex) {
+        return fail(VCM_E_NOMEM, "vcm_build: %s", ex.what());
+    }
+}
+
+vcm_status vcm_compute(vcm_ctx *ctx, const vcm_request *req, float *d_v, uint8_t *d_color, uint32_t *d_bits,
+                       vcm_stats *d_stats, void *stream)
+{
+    float *vv[1] = {d_v};
+    uint8_t *cc[1] = {d_color};
+    uint32_t *bb[1] = {d_bits};
+    return vcm_compute_batch(ctx, req, 1, vv, cc, bb, d_stats, stream);
+}
+
+vcm_status vcm_compute_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, float *const *d_v,
+                             uint8_t *const *d_color, uint32_t *const *d_bits, vcm_stats *d_stats, void *stream)
+{
+    try {
+        vcm_status st = validate_ctx(ctx);
+        if (st != VCM_OK)
+            return st;
+        if (!reqs || n == 0 || !d_v || !d_stats)
+            return fail(VCM_E_ARG, "reqs, d_v and d_stats are required and n > 0");
+        std::vector<Canon> cs(n);
+        for (uint32_t i = 0; i < n; ++i) {
+            if ((st = canonicalise(&reqs[i], cs[i])) != VCM_OK)
+                return st;
+            if (!d_v[i])
+                return fail(VCM_E_ARG, "d_v[%u] is NULL", i);
+            if ((cs[i].flags & VCM_EMIT_BITS) && (!d_bits || !d_bits[i]))
+                return fail(VCM_E_ARG, "VCM_EMIT_BITS needs d_bits[%u]", i);
+        }
+        std::vector<const Canon *> ptrs;
+        std::vector<vcm_tune> shapes;
+        for (auto &c : cs) {
+            ptrs.push_back(&c);
+            shapes.push_back(shape_for(ctx, c));
+        }
+        std::lock_guard<std::mutex> g(ctx->mu);
+        return enqueue_launch(ctx, ctx->direct, ptrs, shapes, d_v, d_color, d_bits, d_stats,
+                              static_cast<cudaStream_t>(stream), true);
+    } catch (const std::exception &ex) {
+        return fail(VCM_E_NOMEM, "vcm_compute_batch: %s", ex.what());
+    }
+}
+
+vcm_status vcm_submit_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, uint64_t *tickets)
+{
+    try {
+        vcm_status st = validate_ctx(ctx);
+        if (st != VCM_OK)
+            return st;
+        if (!reqs || n == 0 || !tickets)
+            return fail(VCM_E_ARG, "reqs and tickets are required and n > 0");
+        std::vector<std::shared_ptr<Ticket>> grp;
+        size_t need = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            auto t = std::make_shared<Ticket>();
+            if ((st = canonicalise(&reqs[i], t->canon)) != VCM_OK)
+                return st;
+            need += t->canon.out_bytes() + 1024;
+            grp.push_back(t);
+        }
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (!ctx->built)
+            return fail(VCM_E_STATE, "vcm_build has not been called for the current scene");
+        if (need > ctx->budget)
+            return fail(VCM_E_NOMEM, "request needs %zu bytes, budget is %zu", need, ctx->budget);
+        const auto now = std::chrono::steady_clock::now();
+        for (uint32_t i = 0; i < n; ++i) {
+            auto &t = grp[i];
+            t->id = ctx->next_ticket++;
+            t->shape = shape_for(ctx, t->canon);
+            t->t_submit = now;
+            ctx->tickets[t->id] = t;
+            tickets[i] = t->id;
+        }
+        ctx->queue.push_back(grp);
+        ctx->cv.notify_all();
+        return VCM_OK;
+    } catch (const std::exception &ex) {
+        return fail(VCM_E_NOMEM, "vcm_submit_batch: %s", ex.what());
+    }
+}
+
+vcm_status vcm_submit(vcm_ctx *ctx, const vcm_request *req, uint64_t *ticket)
+{
+    return vcm_submit_batch(ctx, req, 1, ticket);
+}
+
+vcm_status vcm_poll(vcm_ctx *ctx, uint64_t ticket, int32_t wait_ms)
+{
+    if (!ctx)
+        return fail(VCM_E_ARG, "context is NULL");
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end())
+        return fail(VCM_E_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    std::shared_ptr<Ticket> t = it->second;
+    auto finished = [&] { return t->state == T_DONE || t->state == T_ERROR || t->state == T_CANCELLED; };
+    if (wait_ms < 0)
+        ctx->cv.wait(lk, finished);
+    else if (wait_ms > 0)
+        ctx->cv.wait_for(lk, std::chrono::milliseconds(wait_ms), finished);
+    switch (t->state) {
+    case T_DONE:
+        return VCM_OK;
+    case T_CANCELLED:
+        return fail(VCM_E_CANCELLED, "request %llu was cancelled", (unsigned long long)ticket);
+    case T_ERROR:
+        return fail(t->err, "%s", t->msg.c_str());
+    default:
+        return VCM_PENDING;
+    }
+}
+
+vcm_status vcm_result_get(vcm_ctx *ctx, uint64_t ticket, vcm_result *out)
+{
+    if (!ctx || !out)
+        return fail(VCM_E_ARG, "NULL argument");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end())
+        return fail(VCM_E_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    Ticket &t = *it->second;
+    if (t.state != T_DONE)
+        return fail(VCM_E_STATE, "request %llu is not finished", (unsigned long long)ticket);
+    std::memset(out, 0, sizeof(*out));
+    out->v = t.h_v;
+    out->color = t.h_color;
+    out->bits = t.h_bits;
+    out->d_v = t.d_v;
+    out->d_color = t.d_color;
+    out->d_bits = t.d_bits;
+    out->n_viewpoints = (uint64_t)t.canon.n_vp;
+    out->words_per_viewpoint = (uint32_t)t.canon.words;
+    out->stats = *t.h_stats;
+    out->stats.segments = (unsigned long long)t.canon.n_vp * t.canon.P;
+    out->latency_ms = std::chrono::duration<double, std::milli>(t.t_done - t.t_submit).count();
+    return VCM_OK;
+}
+
+vcm_status vcm_result_release(vcm_ctx *ctx, uint64_t ticket)
+{
+    if (!ctx)
+        return fail(VCM_E_ARG, "context is NULL");
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        auto it = ctx->tickets.find(ticket);
+        if (it == ctx->tickets.end())
+            return fail(VCM_E_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+        Ticket &t = *it->second;
+        if (t.state == T_QUEUED || t.state == T_RUNNING)
+            return fail(VCM_E_STATE, "request %llu is still pending", (unsigned long long)ticket);
+        cudaSetDevice(ctx->device);
+        release_buffers(ctx, t);
+        ctx->tickets.erase(it);
+    }
+    ctx->cv.notify_all();
+    return VCM_OK;
+}
+
+vcm_status vcm_cancel(vcm_ctx *ctx, uint64_t ticket)
+{
+    if (!ctx)
+        return fail(VCM_E_ARG, "context is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end())
+        return fail(VCM_E_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    Ticket &t = *it->second;
+    if (t.state != T_QUEUED)
+        return fail(VCM_E_STATE, "request %llu is already admitted", (unsigned long long)ticket);
+    for (auto qit = ctx->queue.begin(); qit != ctx->queue.end(); ++qit) {
+        auto &grp = *qit;
+        auto pos = std::find_if(grp.begin(), grp.end(), [&](const std::shared_ptr<Ticket> &p) { return p->id == ticket; });
+        if (pos != grp.end()) {
+            grp.erase(pos);
+            if (grp.empty())
+                ctx->queue.erase(qit);
+            break;
+        }
+    }
+    t.state = T_CANCELLED;
+    t.t_done = std::chrono::steady_clock::now();
+    ctx->cv.notify_all();
+    return VCM_OK;
+}
+
+vcm_status vcm_set_slots(vcm_ctx *ctx, uint32_t slots, uint32_t max_batch)
+{
+    vcm_status st = validate_ctx(ctx);
+    if (st != VCM_OK)
+        return st;
+    if (slots < 1 || slots > 16 || max_batch < 1 || max_batch > 4096)
+        return fail(VCM_E_ARG, "slots must be 1..16 and max_batch 1..4096");
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (!scheduler_idle(ctx))
+            return fail(VCM_E_STATE, "requests are still queued or running");
+        ctx->max_batch = max_batch;
+    }
+    stop_scheduler(ctx);
+    for (auto &s : ctx->slots)
+        destroy_slot(*s);
+    ctx->slots.clear();
+    return start_scheduler(ctx, slots);
+}
+
+vcm_status vcm_set_tune(vcm_ctx *ctx, const vcm_tune *tune)
+{
+    if (!ctx || !tune)
+        return fail(VCM_E_ARG, "NULL argument");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (tune->tile_x == 0) {
+        ctx->forced = false;
+        return VCM_OK;
+    }
+    if (tune->tile_x > 256 || tune->tile_y < 1 || tune->tile_y > 256 || tune->patch_k > 16 ||
+        tune->box_cap < 32 || tune->box_cap > 5000)
+        return fail(VCM_E_ARG, "tile sides 1..256, patch_k 0..16, box_cap 32..5000");
+    ctx->forced = true;
+    ctx->forced_tune = *tune;
+    return VCM_OK;
+}
+
+vcm_status vcm_get_tune(vcm_ctx *ctx, const vcm_request *req, vcm_tune *out)
+{
+    if (!ctx || !out)
+        return fail(VCM_E_ARG, "NULL argument");
+    Canon c;
+    vcm_status st = canonicalise(req, c);
+    if (st != VCM_OK)
+        return st;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    *out = shape_for(ctx, c);
+    DevRequest d{};
+    fill_shape(c, *out, d);
+    out->patch_k = (uint32_t)d.k_rows;
+    return VCM_OK;
+}
+
+vcm_status vcm_set_timing_events(vcm_ctx *ctx, void *before_tiles, void *after_tiles)
+{
+    if (!ctx)
+        return fail(VCM_E_ARG, "context is NULL");
+    if ((before_tiles == nullptr) != (after_tiles == nullptr))
+        return fail(VCM_E_ARG, "give both events or neither");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->ev_before = static_cast<cudaEvent_t>(before_tiles);
+    ctx->ev_after = static_cast<cudaEvent_t>(after_tiles);
+    return VCM_OK;
+}
+
+vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vcm_tune *out)
+{
+    try {
+        vcm_status st = validate_ctx(ctx);
+        if (st != VCM_OK)
+            return st;
+        if (!samples || n == 0)
+            return fail(VCM_E_ARG, "samples are required");
+        if (!ctx->built)
+            return fail(VCM_E_STATE, "vcm_build has not been called for the current scene");
+        std::vector<Canon> cs(n);
+        size_t max_vp = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            if ((st = canonicalise(&samples[i], cs[i])) != VCM_OK)
+                return st;
+            cs[i].flags = 0;
+            max_vp = std::max<size_t>(max_vp, (size_t)cs[i].n_vp);
+        }
+        float *d_v = nullptr;
+        vcm_stats *d_stats = nullptr;
+        cudaStream_t s = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CUDA_TRY(cudaMalloc(&d_v, max_vp * sizeof(float)));
+        CUDA_TRY(cudaMalloc(&d_stats, sizeof(vcm_stats)));
+        CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreate(&e0));
+        CUDA_TRY(cudaEventCreate(&e1));
+        const uint32_t tiles[][2] = {{4, 4}, {8, 4}, {8, 8}, {16, 8}, {16, 16}};
+        const uint32_t caps[] = {512, 1024, 2048};
+        const uint32_t ks[] = {0, 4, 8};
+        double best_ms[kTuneClasses];
+        vcm_tune best[kTuneClasses];
+        bool seen[kTuneClasses] = {false};
+        for (int c = 0; c < kTuneClasses; ++c) {
+            best_ms[c] = 1e300;
+            best[c] = default_tune();
+        }
+        std::lock_guard<std::mutex> g(ctx->mu);
+        for (int cls = 0; cls < kTuneClasses; ++cls) {
+            std::vector<const Canon *> mine;
+            for (auto &c : cs)
+                if (tune_class(c.P) == cls)
+                    mine.push_back(&c);
+            if (mine.empty())
+                continue;
+            seen[cls] = true;
+            for (auto &tl : tiles)
+                for (uint32_t cap : caps)
+                    for (uint32_t k : ks) {
+                        vcm_tune t{tl[0], tl[1], k, cap};
+                        double total = 0.0;
+                        for (const Canon *c : mine) {
+                            std::vector<const Canon *> one{c};
+                            std::vector<vcm_tune> sh{t};
+                            float *vv[1] = {d_v};
+                            // one warm launch, one timed launch
+                            for (int rep = 0; rep < 2; ++rep) {
+                                if (rep == 1)
+                                    CUDA_TRY(cudaEventRecord(e0, s));
+                                if ((st = enqueue_launch(ctx, ctx->direct, one, sh, vv, nullptr, nullptr, d_stats, s)) != VCM_OK)
+                                    return st;
+                            }
+                            CUDA_TRY(cudaEventRecord(e1, s));
+                            CUDA_TRY(cudaEventSynchronize(e1));
+                            float ms = 0.f;
+                            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                            total += ms;
+                        }
+                        if (total < best_ms[cls]) {
+                            best_ms[cls] = total;
+                            best[cls] = t;
+                        }
+                    }
+        }
+        for (int cls = 0; cls < kTuneClasses; ++cls)
+            if (seen[cls])
+                ctx->tune[cls] = best[cls];
+        if (out)
+            for (uint32_t i = 0; i < n; ++i)
+                out[i] = ctx->tune[tune_class(cs[i].P)];
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamDestroy(s);
+        cudaFree(d_v);
+        cudaFree(d_stats);
+        return VCM_OK;
+    } catch (const std::exception &ex) {
+        return fail(VCM_E_NOMEM, "vcm_autotune: %s", ex.what());
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// vcm_internal.h -- structures shared by the host runtime (vcm_api.cpp) and
+// the sm_103a kernels (vcm_kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/vcm.h"
+
+namespace vcm {
+
+constexpr int kWarps = 8;                 // warps per block of the tile kernel
+constexpr int kThreads = kWarps * 32;
+constexpr int kMaxPlanes = 32;            // separating planes kept per tile hull
+constexpr float kBand = 1e-6f;            // FP32 slab margin re-decided in FP64
+constexpr int kMaxBoxCap = 5000;          // candidate boxes a tile stages in shared memory
+
+inline size_t tiles_smem_bytes(int box_cap) { return (size_t)box_cap * (32 + 4); }
+
+// Device view of the scene and its uniform-grid index.  Boxes are sorted by
+// grid cell; `boxes[perm]` holds the same boxes with their coordinates
+// permuted into one of the six (u, n, w) target frames, two float4 per box
+// (lo.xyz, hi.xyz).  Permutation 0 is the world frame (x, y, z).
+struct DevScene {
+    const float4 *boxes[6];
+    int n_boxes;
+    int dims;
+    const int *cell_start;     // [n_cells + 1] into the sorted box order
+    const float4 *cell_lo;     // [n_cells] bounds of each cell's boxes (world)
+    const float4 *cell_hi;
+    float gx0, gy0;            // grid origin (world x, y)
+    float cell, inv_cell;
+    int gnx, gny;
+    float overhang;            // how far a cell's bounds reach past the cell
+};
+
+// One canonicalised request (host-computed, lattice-exact coordinates).
+// Target frame: axis 0 = u (patch columns), 1 = n (normal), 2 = w (rows).
+struct DevRequest {
+    int dims;
+    int au, an, aw;            // world axis of u, n, w
+    int perm;                  // index of the box copy in that frame
+    float sn;                  // +1 / -1: side of the normal
+    float p_n;                 // patch coordinate along the normal axis
+    int nu, nw, P, words;
+    float measure;             // patch area (3D) or length (2D), metres
+    int nx, ny, nl;            // viewpoint grid
+    int tile_x, tile_y, tiles_x, tiles_y, n_tiles;
+    int nuc, groups, col_passes, row_passes, k_rows;   // lane mapping
+    const float *u_coord;      // [nu] patch centre coordinate along u
+    const float *w_coord;      // [nw] along w (one 0 in 2D)
+    const float *x_coord;      // [nx] viewpoint x
+    const float *y_coord;      // [ny] viewpoint y
+    const float *z_coord;      // [nl] layer heights (one 0 in 2D)
+    float u_min, u_max, w_min, w_max;
+    float *v_out;
+    uint8_t *color_out;
+    uint32_t *bits_out;
+    vcm_stats *stats;
+    float v_ref_given;
+    int levels;
+    unsigned flags;
+    int box_cap;               // candidate boxes staged in shared memory
+};
+
+// Launch helpers implemented in vcm_kernels.cu.  All are asynchronous on
+// `stream` and return the launch status.
+cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, int n, int dims,
+                              float gx0, float gy0, float cell, int gnx, int gny,
+                              int *d_cell_of, int *d_count, int *d_cursor, int *d_order,
+                              int *d_cell_start, float4 *const *d_perm_boxes, float4 *d_cell_lo,
+                              float4 *d_cell_hi, unsigned *d_overhang_bits, cudaStream_t stream);
+
+// The persistent tile kernel over `n_req` requests (their tiles concatenated,
+// `d_tile_prefix` = exclusive prefix of tiles, n_req + 1 entries).  The
+// kernel draws tiles from `d_work` (zeroed by the caller).  `d_spill` holds
+// grid_blocks * n_boxes ints for candidate lists longer than box_cap.
+cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
+                         int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
+                         int box_cap, int k_rows_max, cudaStream_t stream);
+
+// Colors and edge counts for all viewpoints of n_req requests (grid over the
+// concatenated viewpoints, `d_vp_prefix` = exclusive prefix, n_req + 1).
+cudaError_t launch_quantise(const DevRequest *d_reqs, const long long *d_vp_prefix, int n_req,
+                            long long total_vp, cudaStream_t stream);
+
+// Zero the occlusion-bit buffers of requests with VCM_EMIT_BITS.
+cudaError_t launch_zero_bits(const DevRequest *d_reqs, int n_req, cudaStream_t stream);
+
+// Blocks of the tile kernel that fit on one SM for this shared-memory size.
+int tiles_blocks_per_sm(int box_cap, int k_rows_max);
+
+// One-time per-device setup (constant tables, kernel attributes); must run
+// before any launch is captured into a graph.
+cudaError_t init_device();
+
+}  // namespace vcm

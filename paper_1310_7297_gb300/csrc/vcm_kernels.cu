@@ -1,0 +1,850 @@
+// vcm_kernels.cu -- sm_103a kernels of the visibility color map engine.
+//
+//  * grid build: boxes bucketed by footprint centre into a uniform 2D grid
+//    (count -> scan -> scatter -> per-cell sort -> permuted copies -> bounds);
+//  * tile kernel: persistent blocks draw viewpoint tiles from a queue; each
+//    tile culls the scene against the convex hull of (tile, target) using
+//    the grid, stages the candidates in shared memory with cp.async, and its
+//    warps sweep the tile's viewpoints, lanes over target patch columns and
+//    registers over patch rows, deciding each viewpoint->patch segment by a
+//    float32 slab test (Def. 2 point-to-point visibility; touching blocks,
+//    Def. 4) with an exact float64 re-decision inside a 1e-6 margin band,
+//    then summing A cos(theta)/d^2 (or len cos(theta)/d in 2D) per viewpoint;
+//  * quantise: colors in L levels from v / v_ref (Def. 1 normalisation).
+#include "vcm_internal.h"
+
+#include <cfloat>
+#include <cstdio>
+
+namespace vcm {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
+
+// ---------------------------------------------------------------------------
+// grid build
+// ---------------------------------------------------------------------------
+
+__global__ void k_box_cell(const float *__restrict__ lo, const float *__restrict__ hi, int n,
+                           float gx0, float gy0, float inv_cell, int gnx, int gny,
+                           int *__restrict__ cell_of, int *__restrict__ count)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    float cx = 0.5f * (lo[3 * i + 0] + hi[3 * i + 0]);
+    float cy = 0.5f * (lo[3 * i + 1] + hi[3 * i + 1]);
+    int ix = (int)floorf((cx - gx0) * inv_cell);
+    int iy = (int)floorf((cy - gy0) * inv_cell);
+    ix = min(max(ix, 0), gnx - 1);
+    iy = min(max(iy, 0), gny - 1);
+    int c = iy * gnx + ix;
+    cell_of[i] = c;
+    atomicAdd(&count[c], 1);
+}
+
+// Exclusive scan of count[0..n) into start[0..n] with one block of 1024
+// threads, each owning a contiguous chunk.
+__global__ void k_scan_exclusive(const int *__restrict__ count, int n, int *__restrict__ start)
+{
+    __shared__ int s_part[1024];
+    const int t = threadIdx.x;
+    const int chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int b = min(n, t * chunk), e = min(n, b + chunk);
+    int local = 0;
+    for (int i = b; i < e; ++i)
+        local += count[i];
+    s_part[t] = local;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        int v = (t >= off) ? s_part[t - off] : 0;
+        __syncthreads();
+        s_part[t] += v;
+        __syncthreads();
+    }
+    int run = s_part[t] - local;
+    for (int i = b; i < e; ++i) {
+        start[i] = run;
+        run += count[i];
+    }
+    if (t == (int)blockDim.x - 1)
+        start[n] = s_part[t];
+}
+
+__global__ void k_scatter(const int *__restrict__ cell_of, int n, const int *__restrict__ start,
+                          int *__restrict__ cursor, int *__restrict__ order)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int c = cell_of[i];
+    int pos = start[c] + atomicAdd(&cursor[c], 1);
+    order[pos] = i;
+}
+
+// Deterministic order inside each cell: ascending original box index.
+__global__ void k_sort_cells(const int *__restrict__ start, int n_cells, int *__restrict__ order)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cells)
+        return;
+    int b = start[c], e = start[c + 1];
+    for (int i = b + 1; i < e; ++i) {
+        int v = order[i];
+        int j = i - 1;
+        while (j >= b && order[j] > v) {
+            order[j + 1] = order[j];
+            --j;
+        }
+        order[j + 1] = v;
+    }
+}
+
+__constant__ int c_perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+struct PermPtrs {
+    float4 *p[6];
+};
+
+__global__ void k_write_boxes(const float *__restrict__ lo, const float *__restrict__ hi, int n,
+                              const int *__restrict__ order, PermPtrs out)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n)
+        return;
+    int id = order[s];
+    float L[3] = {lo[3 * id], lo[3 * id + 1], lo[3 * id + 2]};
+    float H[3] = {hi[3 * id], hi[3 * id + 1], hi[3 * id + 2]};
+    for (int p = 0; p < 6; ++p) {
+        const int *a = c_perm[p];
+        out.p[p][2 * s] = make_float4(L[a[0]], L[a[1]], L[a[2]], __int_as_float(id));
+        out.p[p][2 * s + 1] = make_float4(H[a[0]], H[a[1]], H[a[2]], 0.f);
+    }
+}
+
+__global__ void k_cell_bounds(const float4 *__restrict__ boxes, const int *__restrict__ start,
+                              int gnx, int gny, float gx0, float gy0, float cell,
+                              float4 *__restrict__ cell_lo, float4 *__restrict__ cell_hi,
+                              unsigned *__restrict__ overhang_bits)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= gnx * gny)
+        return;
+    float4 lo = make_float4(f_inf(), f_inf(), f_inf(), 0.f);
+    float4 hi = make_float4(-f_inf(), -f_inf(), -f_inf(), 0.f);
+    int b = start[c], e = start[c + 1];
+    for (int s = b; s < e; ++s) {
+        float4 l = boxes[2 * s], h = boxes[2 * s + 1];
+        lo.x = fminf(lo.x, l.x); lo.y = fminf(lo.y, l.y); lo.z = fminf(lo.z, l.z);
+        hi.x = fmaxf(hi.x, h.x); hi.y = fmaxf(hi.y, h.y); hi.z = fmaxf(hi.z, h.z);
+    }
+    cell_lo[c] = lo;
+    cell_hi[c] = hi;
+    if (e > b) {
+        int ix = c % gnx, iy = c / gnx;
+        float x0 = gx0 + ix * cell, y0 = gy0 + iy * cell;
+        float oh = fmaxf(fmaxf(x0 - lo.x, hi.x - (x0 + cell)), fmaxf(y0 - lo.y, hi.y - (y0 + cell)));
+        oh = fmaxf(oh, 0.f);
+        atomicMax(overhang_bits, __float_as_uint(oh));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tile kernel
+// ---------------------------------------------------------------------------
+
+struct __align__(16) Plane {
+    float x, y, z, c;
+};
+
+// n . v, the single evaluation used for hull vertices and box corners alike.
+__device__ __forceinline__ float dot3(float nx, float ny, float nz, float x, float y, float z)
+{
+    return fmaf(nx, x, fmaf(ny, y, nz * z));
+}
+
+// True if the box [lo, hi] lies strictly outside one of the hull's planes.
+// Each plane's offset was raised by more than twice the worst float32 error
+// of dot3 at these coordinate magnitudes, so a box that meets the hull is
+// never reported outside.
+__device__ __forceinline__ bool outside(const Plane *__restrict__ pl, int np, float4 lo, float4 hi)
+{
+    for (int i = 0; i < np; ++i) {
+        Plane p = pl[i];
+        float x = p.x >= 0.f ? lo.x : hi.x;
+        float y = p.y >= 0.f ? lo.y : hi.y;
+        float z = p.z >= 0.f ? lo.z : hi.z;
+        if (dot3(p.x, p.y, p.z, x, y, z) > p.c)
+            return true;
+    }
+    return false;
+}
+
+// Exact re-decision of one segment against one box, in float64.  Inputs are
+// lattice values (multiples of 2^-10 m, |x| <= 2^14 m): differences are
+// exact and every product of two of them needs at most 52 significant bits,
+// so the comparisons below are exact.  The running lower bound en/ed and
+// upper bound xn/xd of the segment parameter t are kept as fractions with
+// positive denominators.
+__device__ __noinline__ bool exact_hit(float qu, float qn, float qw, float pu, float pn, float pw,
+                                       float4 lo, float4 hi)
+{
+    const double q[3] = {qu, qn, qw};
+    const double p[3] = {pu, pn, pw};
+    const double L[3] = {lo.x, lo.y, lo.z};
+    const double H[3] = {hi.x, hi.y, hi.z};
+    double en = 0.0, ed = 1.0, xn = 1.0, xd = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        const double d = p[k] - q[k];
+        const double a = L[k] - q[k];
+        const double b = H[k] - q[k];
+        if (d == 0.0) {
+            if (a > 0.0 || b < 0.0)
+                return false;
+            continue;
+        }
+        double ln, un, den;
+        if (d > 0.0) {
+            ln = a; un = b; den = d;
+        } else {
+            ln = -b; un = -a; den = -d;
+        }
+        if (ln * ed > en * den) {
+            en = ln;
+            ed = den;
+        }
+        if (un * xd < xn * den) {
+            xn = un;
+            xd = den;
+        }
+    }
+    return en * xd <= xn * ed;
+}
+
+__constant__ unsigned char c_tri[56][3];
+
+struct TileSmem {
+    Plane planes[kMaxPlanes];
+    int n_planes;
+    int count;
+    int item;
+    int pad;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Candidate planes of the hull of points P[0..np): for every point triple
+// (3D) or pair (2D) whose plane leaves all points on one side, the outward
+// normal; duplicates from coplanar points keep only their first triple.
+__device__ void hull_planes(int dims, const double (*P)[3], int np, TileSmem &sm)
+{
+    const int t = threadIdx.x;
+    double scale = 0.0;
+    for (int a = 1; a < np; ++a)
+        for (int k = 0; k < 3; ++k)
+            scale = fmax(scale, fabs(P[a][k] - P[0][k]));
+    scale = fmax(scale, 1.0);
+    const int n_cand = (dims == 3) ? 56 : 15;
+    if (t < n_cand) {
+        int i, j, k = -1;
+        double n[3];
+        if (dims == 3) {
+            i = c_tri[t][0]; j = c_tri[t][1]; k = c_tri[t][2];
+            double e1[3], e2[3];
+            for (int c = 0; c < 3; ++c) {
+                e1[c] = P[j][c] - P[i][c];
+                e2[c] = P[k][c] - P[i][c];
+            }
+            n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+            n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+            n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        } else {
+            // pairs (i < j) of 6 points in a fixed order
+            int idx = t;
+            i = 0;
+            while (idx >= np - 1 - i) {
+                idx -= np - 1 - i;
+                ++i;
+            }
+            j = i + 1 + idx;
+            n[0] = -(P[j][1] - P[i][1]);
+            n[1] = P[j][0] - P[i][0];
+            n[2] = 0.0;
+        }
+        const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        const int last = (dims == 3) ? k : j;
+        if (len > 1e-9 * scale * scale) {
+            const double tol = 1e-9 * len * scale;
+            bool pos = false, neg = false, dup = false;
+            for (int l = 0; l < np; ++l) {
+                double s = n[0] * (P[l][0] - P[i][0]) + n[1] * (P[l][1] - P[i][1]) +
+                           n[2] * (P[l][2] - P[i][2]);
+                if (s > tol)
+                    pos = true;
+                if (s < -tol)
+                    neg = true;
+                if (fabs(s) <= tol && l < last && l != i && l != j && l != k)
+                    dup = true;
+            }
+            if (!(pos && neg) && !dup) {
+                for (int side = 0; side < 2; ++side) {
+                    // side 0: n outward (all points at s <= 0); side 1: -n outward
+                    if ((side == 0 && pos) || (side == 1 && neg))
+                        continue;
+                    float nx = (float)((side ? -n[0] : n[0]) / len);
+                    float ny = (float)((side ? -n[1] : n[1]) / len);
+                    float nz = (float)((side ? -n[2] : n[2]) / len);
+                    float c = -f_inf();
+                    for (int l = 0; l < np; ++l)
+                        c = fmaxf(c, dot3(nx, ny, nz, (float)P[l][0], (float)P[l][1], (float)P[l][2]));
+                    c += 0.04f * (fabsf(nx) + fabsf(ny) + fabsf(nz));
+                    int slot = atomicAdd(&sm.n_planes, 1);
+                    if (slot < kMaxPlanes)
+                        sm.planes[slot] = Plane{nx, ny, nz, c};
+                }
+            }
+        }
+    }
+    // the six (four in 2D) axis planes of the hull's bounding box
+    if (t >= 64 && t < 64 + 2 * dims) {
+        int ax = (t - 64) >> 1;
+        bool upper = ((t - 64) & 1) == 0;
+        double m = P[0][ax];
+        for (int l = 1; l < np; ++l)
+            m = upper ? fmax(m, P[l][ax]) : fmin(m, P[l][ax]);
+        float n3[3] = {0.f, 0.f, 0.f};
+        n3[ax] = upper ? 1.f : -1.f;
+        float c = (upper ? (float)m : -(float)m) + 0.04f;
+        int slot = atomicAdd(&sm.n_planes, 1);
+        if (slot < kMaxPlanes)
+            sm.planes[slot] = Plane{n3[0], n3[1], n3[2], c};
+    }
+}
+
+// One viewpoint swept by one warp.  Lane l owns patch column
+// cp * nuc + (l % nuc) and rows (rp * K + m) * groups + l / nuc, m < K.
+// The t-interval of a segment along u depends only on its column, along n
+// only on the viewpoint and along w only on its row, so the u and n parts
+// of the slab test are formed once per box and column, and each row adds
+// its w interval.
+template <int K, bool MIXED>
+__device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const float4 *__restrict__ sbox,
+                                                 int n_smem, const int *__restrict__ spill, int count,
+                                                 const float4 *__restrict__ gbox, float qu, float qn,
+                                                 float qw, bool front, long long vp,
+                                                 unsigned long long &tests, unsigned &rechecks)
+{
+    const int lane = threadIdx.x & 31;
+    const int nuc = R.nuc, G = R.groups;
+    const int c_in = lane % nuc, g = lane / nuc;
+    const bool lane_ok = g < G;
+    const float dn = R.p_n - qn;
+    const float inv_n = __frcp_rn(dn);
+    const bool sgn_n = dn >= 0.f;
+    const bool sgn_w_uni = qw <= R.w_min;    // all rows at dw >= 0 (used when !MIXED)
+    const bool want_bits = (R.flags & VCM_EMIT_BITS) && R.bits_out;
+    float sum = 0.f, comp = 0.f;
+
+    for (int cp = 0; cp < R.col_passes; ++cp) {
+        const int iu = cp * nuc + c_in;
+        const bool col_ok = lane_ok && iu < R.nu;
+        const float pu = R.u_coord[col_ok ? iu : 0];
+        const float du = pu - qu;
+        const float inv_u = __frcp_rn(du);
+        const bool sgn_u = du >= 0.f;
+        for (int rp = 0; rp < R.row_passes; ++rp) {
+            float inv_w[K], clampv[K], pw[K];
+            unsigned valid = 0, sgnw = 0;
+#pragma unroll
+            for (int m = 0; m < K; ++m) {
+                const int iw = (rp * K + m) * G + g;
+                const bool ok = col_ok && iw < R.nw;
+                pw[m] = R.w_coord[ok ? iw : 0];
+                const float dw = pw[m] - qw;
+                inv_w[m] = __frcp_rn(dw);
+                if (dw >= 0.f)
+                    sgnw |= 1u << m;
+                clampv[m] = ok ? 0.f : f_inf();
+                if (ok)
+                    valid |= 1u << m;
+            }
+            unsigned alive = valid;
+            if (!__any_sync(kFull, alive != 0))
+                continue;
+            int nb = 0;
+            for (int i = 0; i < count; ++i) {
+                float4 lo, hi;
+                if (i < n_smem) {
+                    lo = sbox[2 * i];
+                    hi = sbox[2 * i + 1];
+                } else {
+                    const int s = spill[i - n_smem];
+                    lo = __ldg(&gbox[2 * s]);
+                    hi = __ldg(&gbox[2 * s + 1]);
+                }
+                ++nb;
+                const float a_u = lo.x - qu, b_u = hi.x - qu;
+                const float a_n = lo.y - qn, b_n = hi.y - qn;
+                const float a_w = lo.z - qw, b_w = hi.z - qw;
+                const float tnu = (sgn_u ? a_u : b_u) * inv_u;
+                const float tfu = (sgn_u ? b_u : a_u) * inv_u;
+                const float tnn = (sgn_n ? a_n : b_n) * inv_n;
+                const float tfn = (sgn_n ? b_n : a_n) * inv_n;
+                const float pre_e = fmaxf(fmaxf(tnu, tnn), 0.f);
+                const float pre_x = fminf(fminf(tfu, tfn), 1.f);
+                // no row of this column can meet the box: skip the rows
+                if (__all_sync(kFull, alive == 0 || (pre_x - pre_e) < -kBand))
+                    continue;
+                const float near_w = sgn_w_uni ? a_w : b_w;
+                const float far_w = sgn_w_uni ? b_w : a_w;
+#pragma unroll
+                for (int m = 0; m < K; ++m) {
+                    float tnw, tfw;
+                    if (MIXED) {
+                        const bool sp = (sgnw >> m) & 1u;
+                        tnw = (sp ? a_w : b_w) * inv_w[m];
+                        tfw = (sp ? b_w : a_w) * inv_w[m];
+                    } else {
+                        tnw = near_w * inv_w[m];
+                        tfw = far_w * inv_w[m];
+                    }
+                    const float enter = fmaxf(fmaxf(pre_e, tnw), clampv[m]);
+                    const float exit_ = fminf(pre_x, tfw);
+                    const float mv = exit_ - enter;
+                    if (mv >= -kBand) {
+                        bool hit = mv > kBand;
+                        if (!hit) {
+                            hit = exact_hit(qu, qn, qw, pu, R.p_n, pw[m], lo, hi);
+                            ++rechecks;
+                        }
+                        if (hit) {
+                            clampv[m] = f_inf();
+                            alive &= ~(1u << m);
+                        }
+                    }
+                }
+                if (__all_sync(kFull, alive == 0))
+                    break;
+            }
+            tests += (unsigned long long)nb * K;
+            // visible measure of the unblocked rows, and the blocked bits
+#pragma unroll
+            for (int m = 0; m < K; ++m) {
+                if (!((valid >> m) & 1u))
+                    continue;
+                const bool blocked = !((alive >> m) & 1u);
+                const int iw = (rp * K + m) * G + g;
+                if (blocked) {
+                    if (want_bits) {
+                        const int j = iw * R.nu + iu;
+                        atomicOr(&R.bits_out[vp * R.words + (j >> 5)], 1u << (j & 31));
+                    }
+                } else if (front) {
+                    const float ru = qu - pu, rn = qn - R.p_n, rw = qw - pw[m];
+                    const float d2 = fmaf(ru, ru, fmaf(rn, rn, rw * rw));
+                    const float s = R.sn * rn;   // |r| cos(theta)
+                    float term;
+                    if (R.dims == 3) {
+                        const float ir = rsqrtf(d2);
+                        term = R.measure * s * (ir * ir * ir);
+                    } else {
+                        term = R.measure * s / d2;
+                    }
+                    // Neumaier compensated accumulation
+                    const float tsum = sum + term;
+                    if (fabsf(sum) >= fabsf(term))
+                        comp += (sum - tsum) + term;
+                    else
+                        comp += (term - tsum) + sum;
+                    sum = tsum;
+                }
+            }
+        }
+    }
+    float v = sum + comp;
+    // fixed-order butterfly: every lane ends with the same value
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
+
+template <int K>
+__device__ __forceinline__ float sweep_k(const DevRequest &R, const float4 *sbox, int n_smem,
+                                         const int *spill, int count, const float4 *gbox, float qu,
+                                         float qn, float qw, bool front, long long vp,
+                                         unsigned long long &tests, unsigned &rechecks)
+{
+    const bool mixed = !(qw <= R.w_min) && !(qw > R.w_max);
+    if (mixed)
+        return sweep_viewpoint<K, true>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp,
+                                        tests, rechecks);
+    return sweep_viewpoint<K, false>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp,
+                                     tests, rechecks);
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict__ tile_prefix,
+        int n_req, int total_tiles, int *__restrict__ work, int *__restrict__ spill_all, int box_cap)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *s_box = reinterpret_cast<float4 *>(smem_raw);
+    int *s_ids = reinterpret_cast<int *>(smem_raw + (size_t)box_cap * 32);
+    __shared__ TileSmem sm;
+    __shared__ double s_pts[8][3];
+    __shared__ DevRequest s_req;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int *spill = spill_all + (size_t)blockIdx.x * sc.n_boxes;
+
+    for (;;) {
+        if (tid == 0)
+            sm.item = atomicAdd(work, 1);
+        __syncthreads();
+        const int item = sm.item;
+        if (item >= total_tiles)
+            break;
+        // request of this tile: last r with tile_prefix[r] <= item
+        int lo_r = 0, hi_r = n_req - 1;
+        while (lo_r < hi_r) {
+            int mid = (lo_r + hi_r + 1) >> 1;
+            if (tile_prefix[mid] <= item)
+                lo_r = mid;
+            else
+                hi_r = mid - 1;
+        }
+        if (tid == 0)
+            s_req = reqs[lo_r];
+        __syncthreads();
+        const DevRequest &R = s_req;
+        const int t = item - tile_prefix[lo_r];
+        const int per_layer = R.tiles_x * R.tiles_y;
+        const int layer = t / per_layer;
+        const int tt = t - layer * per_layer;
+        const int ty = tt / R.tiles_x, tx = tt - ty * R.tiles_x;
+        const int ix0 = tx * R.tile_x, ix1 = min(R.nx, ix0 + R.tile_x);
+        const int iy0 = ty * R.tile_y, iy1 = min(R.ny, iy0 + R.tile_y);
+        const int tw = ix1 - ix0, tn = tw * (iy1 - iy0);
+        const float zq = R.z_coord[layer];
+        const bool want_bits = (R.flags & VCM_EMIT_BITS) && R.bits_out;
+
+        // side of the target plane: s = sn (q_n - p_n) depends on q_n only
+        float qn_lo, qn_hi;
+        if (R.an == 2) {
+            qn_lo = qn_hi = zq;
+        } else if (R.an == 0) {
+            qn_lo = R.x_coord[ix0]; qn_hi = R.x_coord[ix1 - 1];
+        } else {
+            qn_lo = R.y_coord[iy0]; qn_hi = R.y_coord[iy1 - 1];
+        }
+        const bool any_front = R.sn > 0.f ? (qn_hi - R.p_n > 0.f) : (R.p_n - qn_lo > 0.f);
+        if (!any_front && !want_bits) {
+            for (int i = tid; i < tn; i += kThreads) {
+                const int ix = ix0 + i % tw, iy = iy0 + i / tw;
+                R.v_out[((long long)layer * R.ny + iy) * R.nx + ix] = 0.f;
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // hull of the tile's viewpoints and the target's patch centres
+        if (tid == 0) {
+            sm.n_planes = 0;
+            sm.count = 0;
+            const double X[2] = {R.x_coord[ix0], R.x_coord[ix1 - 1]};
+            const double Y[2] = {R.y_coord[iy0], R.y_coord[iy1 - 1]};
+            for (int c = 0; c < 4; ++c) {
+                s_pts[c][0] = X[c & 1];
+                s_pts[c][1] = Y[c >> 1];
+                s_pts[c][2] = (R.dims == 3) ? (double)zq : 0.0;
+            }
+            if (R.dims == 3) {
+                const double U[2] = {R.u_min, R.u_max}, W[2] = {R.w_min, R.w_max};
+                for (int c = 0; c < 4; ++c) {
+                    s_pts[4 + c][R.au] = U[c & 1];
+                    s_pts[4 + c][R.aw] = W[c >> 1];
+                    s_pts[4 + c][R.an] = R.p_n;
+                }
+            } else {
+                const double U[2] = {R.u_min, R.u_max};
+                for (int c = 0; c < 2; ++c) {
+                    s_pts[4 + c][R.au] = U[c];
+                    s_pts[4 + c][R.an] = R.p_n;
+                    s_pts[4 + c][2] = 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        const int np = (R.dims == 3) ? 8 : 6;
+        hull_planes(R.dims, s_pts, np, sm);
+        __syncthreads();
+        const int n_planes = min(sm.n_planes, kMaxPlanes);
+
+        // walk the grid cells under the hull's footprint
+        {
+            double bx0 = s_pts[0][0], bx1 = s_pts[0][0], by0 = s_pts[0][1], by1 = s_pts[0][1];
+            for (int l = 1; l < np; ++l) {
+                bx0 = fmin(bx0, s_pts[l][0]); bx1 = fmax(bx1, s_pts[l][0]);
+                by0 = fmin(by0, s_pts[l][1]); by1 = fmax(by1, s_pts[l][1]);
+            }
+            const float oh = sc.overhang;
+            int cx0 = (int)floorf(((float)bx0 - oh - sc.gx0) * sc.inv_cell) - 1;
+            int cx1 = (int)floorf(((float)bx1 + oh - sc.gx0) * sc.inv_cell) + 1;
+            int cy0 = (int)floorf(((float)by0 - oh - sc.gy0) * sc.inv_cell) - 1;
+            int cy1 = (int)floorf(((float)by1 + oh - sc.gy0) * sc.inv_cell) + 1;
+            cx0 = max(cx0, 0); cy0 = max(cy0, 0);
+            cx1 = min(cx1, sc.gnx - 1); cy1 = min(cy1, sc.gny - 1);
+            const int wcx = cx1 - cx0 + 1;
+            const int ncell = (cx1 >= cx0 && cy1 >= cy0) ? wcx * (cy1 - cy0 + 1) : 0;
+            const float4 *world = sc.boxes[0];
+            for (int c = tid; c < ncell; c += kThreads) {
+                const int cell = (cy0 + c / wcx) * sc.gnx + cx0 + c % wcx;
+                const int b = sc.cell_start[cell], e = sc.cell_start[cell + 1];
+                if (b == e || outside(sm.planes, n_planes, sc.cell_lo[cell], sc.cell_hi[cell]))
+                    continue;
+                for (int s = b; s < e; ++s) {
+                    if (outside(sm.planes, n_planes, world[2 * s], world[2 * s + 1]))
+                        continue;
+                    const int pos = atomicAdd(&sm.count, 1);
+                    if (pos < box_cap)
+                        s_ids[pos] = s;
+                    else
+                        spill[pos - box_cap] = s;
+                }
+            }
+        }
+        __syncthreads();
+        const int count = sm.count;
+        const int n_smem = min(count, box_cap);
+        const float4 *gbox = sc.boxes[R.perm];
+        for (int i = tid; i < n_smem; i += kThreads) {
+            const float4 *src = gbox + 2 * s_ids[i];
+            cp_async16(&s_box[2 * i], src);
+            cp_async16(&s_box[2 * i + 1], src + 1);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+
+        // sweep: each warp takes viewpoints of the tile in turn
+        unsigned long long tests = 0;
+        unsigned rechecks = 0;
+        float vmax = 0.f;
+        for (int vi = warp; vi < tn; vi += kWarps) {
+            const int ix = ix0 + vi % tw, iy = iy0 + vi / tw;
+            const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
+            const float qw3[3] = {R.x_coord[ix], R.y_coord[iy], zq};
+            const float qu = qw3[R.au], qn = qw3[R.an], qw = (R.dims == 3) ? qw3[R.aw] : 0.f;
+            const bool front = R.sn * (qn - R.p_n) > 0.f;
+            if (!front && !want_bits) {
+                if (lane == 0)
+                    R.v_out[vp] = 0.f;
+                continue;
+            }
+            float v;
+            switch (R.k_rows) {
+            case 1: v = sweep_k<1>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, tests, rechecks); break;
+            case 2: v = sweep_k<2>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, tests, rechecks); break;
+            case 4: v = sweep_k<4>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, tests, rechecks); break;
+            case 8: v = sweep_k<8>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, tests, rechecks); break;
+            default: v = sweep_k<16>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, tests, rechecks); break;
+            }
+            if (!front)
+                v = 0.f;
+            if (lane == 0)
+                R.v_out[vp] = v;
+            vmax = fmaxf(vmax, v);
+        }
+        // per-tile counters
+        if (lane == 0) {
+            atomicMax(&R.stats->vmax_bits, __float_as_uint(vmax));
+            atomicAdd(&R.stats->slab_tests, tests * 32ull);
+        }
+        for (int off = 16; off > 0; off >>= 1)
+            rechecks += __shfl_xor_sync(kFull, rechecks, off);
+        if (lane == 0 && rechecks)
+            atomicAdd(&R.stats->rechecked, (unsigned long long)rechecks);
+        if (tid == 0)
+            atomicAdd(&R.stats->boxes_listed, (unsigned long long)count);
+        __syncthreads();
+    }
+}
+
+// Clear the occlusion-bit buffers of the requests that asked for bits
+// (bits are set with atomicOr by the tile kernel).
+__global__ void k_zero_bits(const DevRequest *__restrict__ reqs, int n_req)
+{
+    for (int r = 0; r < n_req; ++r) {
+        const DevRequest &R = reqs[r];
+        if (!(R.flags & VCM_EMIT_BITS) || !R.bits_out)
+            continue;
+        const long long n = (long long)R.nx * R.ny * R.nl * R.words;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x)
+            R.bits_out[i] = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// colors
+// ---------------------------------------------------------------------------
+
+__global__ void k_quantise(const DevRequest *__restrict__ reqs, const long long *__restrict__ vp_prefix,
+                           int n_req, long long total)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        int lo_r = 0, hi_r = n_req - 1;
+        while (lo_r < hi_r) {
+            int mid = (lo_r + hi_r + 1) >> 1;
+            if (vp_prefix[mid] <= i)
+                lo_r = mid;
+            else
+                hi_r = mid - 1;
+        }
+        const DevRequest &R = reqs[lo_r];
+        const long long local = i - vp_prefix[lo_r];
+        const float vref = R.v_ref_given > 0.f ? R.v_ref_given : __uint_as_float(R.stats->vmax_bits);
+        const float v = R.v_out[local];
+        const int L = R.levels;
+        unsigned char c = 0;
+        bool edge = false;
+        if (v > 0.f && vref > 0.f) {
+            const float x = (float)(L - 1) * v / vref;
+            const int f = (int)floorf(x);
+            c = (unsigned char)(1 + min(L - 2, f));
+            const float r = rintf(x);
+            edge = r >= 1.f && r <= (float)(L - 2) && fabsf(x - r) <= 1e-5f * x;
+        }
+        if (R.color_out)
+            R.color_out[local] = c;
+        const unsigned ballot = __ballot_sync(__activemask(), edge);
+        if (edge && (threadIdx.x & 31) == (unsigned)(__ffs(ballot) - 1))
+            atomicAdd(&R.stats->edge_cells, (unsigned)__popc(ballot));
+        if (local == 0)
+            R.stats->v_ref = vref;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+
+cudaError_t init_device()
+{
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 0 && dev < 64 && done[dev])
+        return cudaSuccess;
+    unsigned char tri[56][3];
+    int n = 0;
+    for (int i = 0; i < 8; ++i)
+        for (int j = i + 1; j < 8; ++j)
+            for (int k = j + 1; k < 8; ++k) {
+                tri[n][0] = (unsigned char)i;
+                tri[n][1] = (unsigned char)j;
+                tri[n][2] = (unsigned char)k;
+                ++n;
+            }
+    if ((e = cudaMemcpyToSymbol(c_tri, tri, sizeof(tri))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tiles_smem_bytes(kMaxBoxCap))) != cudaSuccess)
+        return e;
+    if (dev >= 0 && dev < 64)
+        done[dev] = true;
+    return cudaSuccess;
+}
+
+cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, int n, int dims,
+                              float gx0, float gy0, float cell, int gnx, int gny,
+                              int *d_cell_of, int *d_count, int *d_cursor, int *d_order,
+                              int *d_cell_start, float4 *const *d_perm_boxes, float4 *d_cell_lo,
+                              float4 *d_cell_hi, unsigned *d_overhang_bits, cudaStream_t stream)
+{
+    (void)dims;
+    const int n_cells = gnx * gny;
+    const int tb = 256;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d_count, 0, sizeof(int) * n_cells, stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(d_cursor, 0, sizeof(int) * n_cells, stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(d_overhang_bits, 0, sizeof(unsigned), stream)) != cudaSuccess) return e;
+    if (n > 0)
+        k_box_cell<<<(n + tb - 1) / tb, tb, 0, stream>>>(d_lo_world, d_hi_world, n, gx0, gy0, 1.0f / cell,
+                                                          gnx, gny, d_cell_of, d_count);
+    k_scan_exclusive<<<1, 1024, 0, stream>>>(d_count, n_cells, d_cell_start);
+    if (n > 0) {
+        k_scatter<<<(n + tb - 1) / tb, tb, 0, stream>>>(d_cell_of, n, d_cell_start, d_cursor, d_order);
+        k_sort_cells<<<(n_cells + tb - 1) / tb, tb, 0, stream>>>(d_cell_start, n_cells, d_order);
+        PermPtrs pp;
+        for (int p = 0; p < 6; ++p)
+            pp.p[p] = d_perm_boxes[p];
+        k_write_boxes<<<(n + tb - 1) / tb, tb, 0, stream>>>(d_lo_world, d_hi_world, n, d_order, pp);
+    }
+    k_cell_bounds<<<(n_cells + tb - 1) / tb, tb, 0, stream>>>(d_perm_boxes[0], d_cell_start, gnx, gny,
+                                                               gx0, gy0, cell, d_cell_lo, d_cell_hi,
+                                                               d_overhang_bits);
+    return cudaGetLastError();
+}
+
+int tiles_blocks_per_sm(int box_cap, int k_rows_max)
+{
+    (void)k_rows_max;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tiles, kThreads, tiles_smem_bytes(box_cap)) !=
+        cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
+                         int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
+                         int box_cap, int k_rows_max, cudaStream_t stream)
+{
+    (void)k_rows_max;
+    if (total_tiles <= 0)
+        return cudaSuccess;
+    if (box_cap < 1 || box_cap > kMaxBoxCap)
+        return cudaErrorInvalidValue;
+    const size_t smem = tiles_smem_bytes(box_cap);
+    k_tiles<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles,
+                                                     d_work, d_spill, box_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_bits(const DevRequest *d_reqs, int n_req, cudaStream_t stream)
+{
+    if (n_req <= 0)
+        return cudaSuccess;
+    k_zero_bits<<<152 * 4, 256, 0, stream>>>(d_reqs, n_req);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quantise(const DevRequest *d_reqs, const long long *d_vp_prefix, int n_req,
+                            long long total_vp, cudaStream_t stream)
+{
+    if (total_vp <= 0)
+        return cudaSuccess;
+    long long blocks = (total_vp + 255) / 256;
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    k_quantise<<<(int)blocks, 256, 0, stream>>>(d_reqs, d_vp_prefix, n_req, total_vp);
+    return cudaGetLastError();
+}
+
+}  // namespace vcm

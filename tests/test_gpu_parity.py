@@ -1,0 +1,313 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bits must match exactly, v within 1e-5 relative, colors exactly except for
+cells within 2e-5 of a bin edge.  Sizes span many tiles with ragged tails;
+the full-size 3D workload is checked on sampled viewpoints.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import compare_bits, compare_colors, compare_v, full_parity, gpu_run
+from helpers import U, req2, req3, scene
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1310_7297_gb300 import Context
+
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def load(ctx, sc, cell=0.0):
+    ctx.load_scene(sc)
+    ctx.vcm_build(cell)
+
+
+# ---------------------------------------------------------------------------
+# the workloads
+# ---------------------------------------------------------------------------
+
+def test_workload_2d_full(ctx):
+    sc, req = synth.workload_2d()
+    load(ctx, sc)
+    gv, gb, st, err, mism = full_parity(ctx, sc, req)
+    assert (gv > 0).sum() > 1000
+    assert st["rechecked"] >= 0 and st["slab_tests"] > 0
+
+
+def test_workload_3d_reduced_full(ctx):
+    sc, req = synth.workload_3d(seed=7, grid=40, layers=5, patches=(32, 16), n_boxes=800, half_m=400.0,
+                                n_components=6, sigma_m=(30.0, 120.0))
+    load(ctx, sc, 40.0)
+    gv, gb, st, err, mism = full_parity(ctx, sc, req)
+    assert (gv > 0).sum() > 500 and gb.any()
+
+
+def test_workload_3d_full_size_sampled(ctx):
+    """512 x 512 x 5 viewpoints, 5,000 boxes, 32 x 16 patches, in the launch
+    configuration the benchmark times; the oracle checks 1,200 viewpoints."""
+    sc, req = synth.workload_3d()
+    load(ctx, sc)
+    gv, gc, gb, st = gpu_run(ctx, req, bits=True)
+    n = gv.shape[0]
+    rng = np.random.default_rng(11)
+    nz = np.nonzero(gv > 0)[0]
+    idx = np.unique(np.concatenate([rng.choice(n, 600, replace=False), rng.choice(nz, 600, replace=False)]))
+    ov, ob = O.run(sc, req, indices=idx, bits=True)
+    compare_bits(ob, gb[idx], "full-size sample")
+    compare_v(ov, gv[idx], "full-size sample")
+    # colors follow the device's own v and v_ref = max v
+    assert st["v_ref"] == pytest.approx(float(gv.max()), rel=0, abs=0)
+    assert (gc[gv == 0] == 0).all() and (gc[gv > 0] >= 1).all() and gc.max() == req["color_levels"] - 1
+    assert st["slab_tests"] > 0
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_empty_scene(ctx):
+    sc = scene(3, [])
+    r = req3((0, 0, 30 * U), pu=8, pw=4, origin=(-50 * U, -50 * U), step=(10 * U, 10 * U), n=(10, 10),
+             layers=(2 * U, 40 * U))
+    load(ctx, sc)
+    gv, gb, st, err, mism = full_parity(ctx, sc, r)
+    assert not gb.any() and (gv > 0).any()
+
+
+def test_full_wall_and_inside_box(ctx):
+    sc = scene(3, [((-2000 * U, 2 * U, -10 * U), (2000 * U, 3 * U, 2000 * U)),
+                   ((-40 * U, -40 * U, 0), (-30 * U, -30 * U, 10 * U))])
+    r = req3((0, 0, 30 * U), pu=8, pw=4, origin=(-64 * U, -60 * U), step=(16 * U, 16 * U), n=(8, 8),
+             layers=(2 * U, 30 * U, 70 * U))
+    load(ctx, sc)
+    gv, gb, st, err, mism = full_parity(ctx, sc, r)
+    assert (gv == 0).all()
+
+
+@pytest.mark.parametrize("patches", [(1, 1), (7, 3), (8, 4), (16, 8), (40, 5), (48, 20), (64, 32), (33, 1)])
+def test_patch_shapes_and_ragged_tiles(ctx, patches):
+    sc, _ = synth.workload_3d(seed=3, grid=8, layers=1, n_boxes=400, half_m=250.0, n_components=4,
+                              sigma_m=(20.0, 80.0))
+    r = req3((0, 0, 30 * U), width=20 * U, height=10 * U, pu=patches[0], pw=patches[1],
+             origin=(-240 * U, -240 * U), step=(37 * U, 23 * U), n=(13, 21), layers=(1741, 31 * U, 45 * U))
+    load(ctx, sc, 30.0)
+    full_parity(ctx, sc, r)
+
+
+@pytest.mark.parametrize("axes", [(2, 4, 0), (3, 5, 1), (0, 4, 3), (1, 2, 4), (0, 3, 5)])
+def test_target_orientations(ctx, axes):
+    """u, w and the normal along every axis, both signs (incl. a horizontal
+    target facing up or down, seen from layers on both sides)."""
+    rng = np.random.default_rng(sum(axes))
+    lo = rng.integers(-150 * U, 130 * U, size=(120, 3))
+    lo[:, 2] = rng.integers(0, 20 * U, size=120)
+    hi = lo + rng.integers(3 * U, 25 * U, size=(120, 3))
+    c = np.array([0, 0, 30 * U])
+    keep = ~np.all((lo <= c + 12 * U) & (c - 12 * U <= hi), axis=1)
+    sc = scene(3, list(zip(lo[keep].tolist(), hi[keep].tolist())))
+    r = req3((0, 0, 30 * U), axis_u=axes[0], axis_w=axes[1], normal=axes[2], width=12 * U, height=6 * U,
+             pu=12, pw=6, origin=(-160 * U, -160 * U), step=(20 * U, 20 * U), n=(16, 16),
+             layers=(2 * U, 30 * U, 60 * U))
+    load(ctx, sc, 25.0)
+    full_parity(ctx, sc, r)
+
+
+def test_2d_orientations_and_long_segment(ctx):
+    rng = np.random.default_rng(4)
+    lo = rng.integers(-300 * U, 280 * U, size=(80, 3))
+    lo[:, 2] = 0
+    hi = lo + rng.integers(2 * U, 20 * U, size=(80, 3))
+    hi[:, 2] = 0
+    keep = ~np.all((lo[:, :2] <= 30 * U) & (-30 * U <= hi[:, :2]), axis=1)
+    sc = scene(2, list(zip(lo[keep].tolist(), hi[keep].tolist())))
+    load(ctx, sc, 20.0)
+    for (au, nr, pu) in [(0, 2, 100), (2, 1, 37), (3, 0, 64), (1, 3, 5)]:
+        r = req2((0, 0), axis_u=au, normal=nr, width=40 * U, pu=pu, origin=(-300 * U, -300 * U),
+                 step=(15 * U, 12 * U), n=(40, 50))
+        full_parity(ctx, sc, r)
+
+
+def test_viewpoints_on_target_plane_and_exact_coincidences(ctx):
+    """Viewpoint rows exactly on the target plane (d_n = 0) and viewpoint
+    columns equal to patch columns (d_u = 0), with box faces on the same
+    lattice lines: the zero-direction and touching cases of the slab test."""
+    boxes = []
+    for i in range(-6, 7):
+        for j in (-3, 2, 5):
+            boxes.append(((i * 8 * U, j * 8 * U, 0), (i * 8 * U + 4 * U, j * 8 * U + 4 * U, (i % 4 + 1) * 8 * U)))
+    sc = scene(3, boxes)
+    # patch columns at x = -15..15 step 2 (odd metres), rows at z = 21..39
+    r = req3((0, 0, 30 * U), width=32 * U, height=20 * U, pu=16, pw=10, origin=(-64 * U, -40 * U),
+             step=(2 * U, 4 * U), n=(64, 20), layers=(21 * U, 30 * U, 8 * U))
+    load(ctx, sc, 16.0)
+    gv, gb, st, err, mism = full_parity(ctx, sc, r)
+    assert st["rechecked"] > 0   # exact touches land in the band
+
+
+def test_tie_heavy_integer_scene(ctx):
+    """Everything on whole metres: many segments pass exactly through box
+    edges and corners, so the float64 re-decision carries the result."""
+    rng = np.random.default_rng(9)
+    lo = rng.integers(-40, 36, size=(150, 3)) * U
+    lo[:, 2] = rng.integers(0, 10, size=150) * U
+    hi = lo + rng.integers(1, 6, size=(150, 3)) * U
+    keep = ~np.all((lo <= np.array([9, 1, 27]) * U) & (np.array([-9, -1, 13]) * U <= hi), axis=1)
+    sc = scene(3, list(zip(lo[keep].tolist(), hi[keep].tolist())))
+    r = req3((0, 0, 20 * U), width=16 * U, height=12 * U, pu=8, pw=6, origin=(-40 * U, -40 * U),
+             step=(2 * U, 2 * U), n=(40, 40), layers=(0, 5 * U, 20 * U))
+    load(ctx, sc, 8.0)
+    gv, gb, st, err, mism = full_parity(ctx, sc, r)
+    assert st["rechecked"] > 0
+
+
+def test_large_coordinates_and_thin_boxes(ctx):
+    base = 16000 * U
+    rng = np.random.default_rng(2)
+    lo = rng.integers(base - 300 * U, base - 40 * U, size=(60, 3))
+    lo[:, 2] = 0
+    ext = rng.integers(0, 15 * U, size=(60, 3))
+    ext[::3, 0] = 0   # zero-thickness walls
+    hi = np.minimum(lo + ext, 16384 * U)
+    sc = scene(3, list(zip(lo.tolist(), hi.tolist())))
+    r = req3((base, base, 20 * U), normal=3, width=10 * U, height=6 * U, pu=10, pw=6,
+             origin=(base - 320 * U, base - 320 * U), step=(20 * U, 20 * U), n=(16, 16), layers=(1 * U, 18 * U))
+    load(ctx, sc, 30.0)
+    full_parity(ctx, sc, r)
+
+
+def test_given_v_ref_and_levels(ctx):
+    sc, req = synth.workload_2d(seed=5, grid=48, samples=32, n_rects=60)
+    load(ctx, sc)
+    for levels, vref in [(2, 0.0), (256, 0.0), (16, 0.05), (8, 100.0)]:
+        r = dict(req, color_levels=levels, v_ref=vref)
+        gv, gc, gb, st = gpu_run(ctx, r, bits=False)
+        ov = O.run(sc, r)
+        compare_v(ov, gv)
+        compare_colors(ov, gc, levels, vref)
+        if vref > 0:
+            assert st["v_ref"] == pytest.approx(vref, rel=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# launch shapes, spill, batching, scheduling: identical results
+# ---------------------------------------------------------------------------
+
+def _bits_and_v(ctx, req):
+    gv, gc, gb, st = gpu_run(ctx, req, bits=True)
+    return gv, gc, gb
+
+
+def test_launch_shapes_and_spill_give_identical_results(ctx):
+    sc, req = synth.workload_3d(seed=12, grid=48, layers=2, patches=(16, 8), n_boxes=1500, half_m=300.0,
+                                n_components=5, sigma_m=(30.0, 100.0))
+    load(ctx, sc, 30.0)
+    ref = _bits_and_v(ctx, req)
+    try:
+        for shape in [(1, 1, 0, 1024), (3, 5, 2, 64), (16, 16, 16, 2048), (8, 8, 1, 32), (4, 4, 4, 48)]:
+            ctx.vcm_set_tune(*shape)
+            got = _bits_and_v(ctx, req)
+            assert np.array_equal(got[0], ref[0]), shape     # bit-identical v
+            assert np.array_equal(got[1], ref[1]), shape
+            assert np.array_equal(got[2], ref[2]), shape
+    finally:
+        ctx.vcm_set_tune(0)
+    ov, ob = O.run(sc, req, bits=True)
+    compare_bits(ob, ref[2])
+    compare_v(ov, ref[0])
+
+
+def test_batch_equals_single_requests(ctx):
+    import torch
+
+    from paper_1310_7297_gb300 import n_viewpoints, words
+
+    sc, reqs = synth.workload_batched(seed=8, n_requests=6, n_boxes=3000, min_side=3, max_side=6)
+    load(ctx, sc, 50.0)
+    singles = [_bits_and_v(ctx, dict(r, flags=1)) for r in reqs]
+    dev = torch.device("cuda", 0)
+    vs = [torch.empty(n_viewpoints(r), device=dev) for r in reqs]
+    cs = [torch.empty(n_viewpoints(r), dtype=torch.uint8, device=dev) for r in reqs]
+    bs = [torch.empty(n_viewpoints(r) * words(r), dtype=torch.int32, device=dev) for r in reqs]
+    st = torch.empty(48 * len(reqs), dtype=torch.uint8, device=dev)
+    ctx.vcm_compute_batch([dict(r, flags=1) for r in reqs], [t.data_ptr() for t in vs], [t.data_ptr() for t in cs],
+                          [t.data_ptr() for t in bs], st.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for i, r in enumerate(reqs):
+        assert np.array_equal(vs[i].cpu().numpy().astype(np.float64), singles[i][0])
+        assert np.array_equal(cs[i].cpu().numpy(), singles[i][1])
+        assert np.array_equal(bs[i].cpu().numpy().view(np.uint32).reshape(n_viewpoints(r), -1), singles[i][2])
+    # and one of them against the oracle on a sample
+    r = reqs[0]
+    idx = np.arange(0, n_viewpoints(r), 7)
+    ov, ob = O.run(sc, r, indices=idx, bits=True)
+    compare_bits(ob, singles[0][2][idx])
+    compare_v(ov, singles[0][0][idx])
+
+
+def test_submit_poll_matches_direct(ctx):
+    sc, reqs = synth.workload_batched(seed=9, n_requests=5, n_boxes=2000, min_side=3, max_side=6)
+    load(ctx, sc, 50.0)
+    tickets = [ctx.vcm_submit(dict(r, flags=1)) for r in reqs]
+    for t, r in zip(tickets, reqs):
+        assert ctx.vcm_poll(t, -1) == 0
+        v, c, b, st = ctx.vcm_result_get(t)
+        ref = _bits_and_v(ctx, dict(r, flags=1))
+        assert np.array_equal(v.astype(np.float64), ref[0]) and np.array_equal(c, ref[1])
+        assert np.array_equal(b, ref[2])
+        assert st["latency_ms"] > 0 and st["segments"] == len(v) * r["patches_u"] * r["patches_w"]
+        ctx.vcm_result_release(t)
+
+
+def test_deterministic_repeat(ctx):
+    sc, req = synth.workload_2d(seed=3)
+    load(ctx, sc)
+    a = _bits_and_v(ctx, req)
+    b = _bits_and_v(ctx, req)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+# ---------------------------------------------------------------------------
+# argument checking through the C ABI
+# ---------------------------------------------------------------------------
+
+def test_argument_errors(ctx):
+    from paper_1310_7297_gb300 import VcmError
+
+    sc, req = synth.workload_2d(seed=2, grid=16)
+    load(ctx, sc)
+    ctx.compute(dict(req, center=[1, 0, 0]))     # one lattice unit off centre is fine
+    for r, st in [(dict(req, dims=4), -1), (dict(req, normal=0), -1), (dict(req, color_levels=1), -1),
+                  (dict(req, grid_step=[0, 8000]), -1), (dict(req, patches_u=0), -1),
+                  (dict(req, flags=8), -1)]:
+        with pytest.raises(VcmError) as e:
+            ctx.compute(r)
+        assert e.value.status == st
+    with pytest.raises(VcmError) as e:
+        ctx.vcm_scene_load_mem(np.array([[0.1, 0.0]], np.float32), np.array([[1.0, 1.0]], np.float32), 2)
+    assert e.value.status == -1     # 0.1 m is not on the 2^-10 m lattice
+    with pytest.raises(VcmError) as e:
+        ctx.vcm_scene_load_mem(np.array([[np.nan, 0.0]], np.float32), np.array([[1.0, 1.0]], np.float32), 2)
+    assert e.value.status == -1
+    with pytest.raises(VcmError) as e:
+        ctx.vcm_scene_load_mem(np.array([[2.0, 0.0]], np.float32), np.array([[1.0, 1.0]], np.float32), 2)
+    assert e.value.status == -1     # lo > hi
+    # a new scene must be built before use
+    ctx.vcm_scene_load_mem(np.array([[2.0, 2.0]], np.float32), np.array([[3.0, 3.0]], np.float32), 2)
+    with pytest.raises(VcmError) as e:
+        ctx.compute(req)
+    assert e.value.status == -7
+    with pytest.raises(VcmError) as e:
+        ctx.vcm_submit(req)
+    assert e.value.status == -7
