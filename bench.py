@@ -1,0 +1,496 @@
+#!/usr/bin/env python3
+"""Benchmark of the visibility color map (VCM) path on GB300.
+
+Workload (one step = one whole VCM: grid-index cull, slab tests, visible
+measure, quantisation): the 3D plain VCM - 512 x 512 viewpoints at 1.7 m
+plus 4 layers spaced 10 m, 5,000 boxes (footprints 10-60 m, lognormal
+heights, median 20 m, sigma 0.6, centres from a 16-component Gaussian
+mixture over 2 km x 2 km), a 20 m x 10 m target at 30 m split into 32 x 16
+patches, 16 color levels.  Seeded synthetic inputs stand in for the paper's
+city datasets.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+Under torchrun each rank runs its own full copy of the workload (weak
+scaling, no data-path collective) and the slowest rank's time is reported.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "viewpoint-patch occlusion tests/sec and VCM cells/sec at ≤1e-5 rel err; p50/p99 latency"
+UNIT = "segments/s"
+WORKLOAD = "3D plain VCM: 512x512 viewpoints x 5 layers, 5,000 mixture boxes over 2 km, 20x10 m target, 32x16 patches"
+# Lane-level operations of one separable slab test in the row loop of the
+# tile kernel: 2 FMUL (w interval), 3 FMNMX (enter/exit), 1 FADD (margin),
+# 1 FSETP (band compare).
+OPS_PER_SLAB_TEST = 7
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def alu_peak_ops(sm_count, mhz):
+    """Issue-limited lane-operation rate: 4 schedulers x 32 lanes per SM per clock."""
+    return sm_count * 4 * 32 * mhz * 1e6
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        rows = []
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0]:
+                continue
+            rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def reduce_max(x, pg, device=None):
+    """Largest value of x over all ranks (identity without a process group)."""
+    if pg is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(scene, req, seconds, seed=0):
+    """Segments/s of the CPU oracle on a seeded random viewpoint sample sized
+    for about `seconds` of work, on all host cores."""
+    from oracle import oracle as O
+
+    O.build()
+    n = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
+    P = req["patches_u"] * req["patches_w"]
+    rng = np.random.default_rng(seed)
+    probe = np.sort(rng.choice(n, 64, replace=False))
+    t0 = time.perf_counter()
+    O.run(scene, req, indices=probe)
+    dt = time.perf_counter() - t0
+    m = int(min(n, max(64, 64 * seconds / max(dt, 1e-6))))
+    idx = np.sort(rng.choice(n, m, replace=False))
+    t0 = time.perf_counter()
+    O.run(scene, req, indices=idx)
+    dt = time.perf_counter() - t0
+    return {"value": m * P / dt, "cells_per_s": m / dt, "seconds": dt, "viewpoints": m,
+            "cores": O.default_threads()}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import synth
+
+    scene, req = synth.workload_3d()
+    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup):
+        oracle_rate(scene, req, per_step / 4, seed=100 + i)
+    rates, secs, vps, cores = [], [], 0, 1
+    for i in range(args.steps):
+        r = oracle_rate(scene, req, per_step, seed=i)
+        rates.append(r["value"])
+        secs.append(r["seconds"])
+        vps += r["viewpoints"]
+        cores = r["cores"]
+    value = float(np.mean(rates))
+    P = req["patches_u"] * req["patches_w"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(scene, req),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d random viewpoints of the workload over %d steps (%d patches each)"
+                                   % (vps, args.steps, P)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(scene, req):
+    n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
+    return {"workload": WORKLOAD, "viewpoints": n_vp, "grid": [req["grid_nx"], req["grid_ny"]],
+            "layers_m": [z / 1024 for z in req["layer_z"]], "patches": [req["patches_u"], req["patches_w"]],
+            "boxes": scene.n, "scene_digest": scene.digest(), "color_levels": req["color_levels"],
+            "segments_per_step": n_vp * req["patches_u"] * req["patches_w"],
+            "l2": "512 MB buffer written between timed steps", "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+
+    import synth
+    from paper_1310_7297_gb300 import Context, stats_from_tensor
+    from paper_1310_7297_gb300 import build as B
+
+    world, rank, local = dist_setup()
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    scene, req = synth.workload_3d()
+    n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
+    P = req["patches_u"] * req["patches_w"]
+    seg = n_vp * P
+    ctx = Context(local)
+    ctx.load_scene(scene)
+    ctx.vcm_build(0.0)
+    stream = torch.cuda.current_stream(dev)
+    v = torch.empty(n_vp, dtype=torch.float32, device=dev)
+    col = torch.empty(n_vp, dtype=torch.uint8, device=dev)
+    st = torch.empty(48, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.vcm_compute(req, v.data_ptr(), col.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    uuid = None
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = u[4:] if u.startswith("GPU-") else u
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    K = args.steps
+    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    kb = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ka = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.zero_()
+        ctx.vcm_set_timing_events(kb[i], ka[i])
+        s_ev[i].record(stream)
+        step()
+        e_ev[i].record(stream)
+    torch.cuda.synchronize()
+    ctx.vcm_set_timing_events(None, None)
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(s_ev, e_ev)]
+    kern_ms = [b.elapsed_time(a) for b, a in zip(kb, ka)]
+    total_ms = reduce_max(float(sum(step_ms)), pg, dev)
+    if pg:
+        pg.barrier()
+    stats = stats_from_tensor(st)
+
+    # end to end through the public API with host buffers: scene upload,
+    # index build, submit, poll, result copy back to the host
+    lo = torch.from_numpy(scene.lo_f32()[:, :3].copy()).pin_memory().numpy()
+    hi = torch.from_numpy(scene.hi_f32()[:, :3].copy()).pin_memory().numpy()
+    e2e_ms = []
+    for i in range(args.warmup + K):
+        t0 = time.perf_counter()
+        ctx.vcm_scene_load_mem(lo, hi, 3)
+        ctx.vcm_build(0.0)
+        t = ctx.vcm_submit(req)
+        ctx.vcm_poll(t, -1)
+        hv, hc, _, _ = ctx.vcm_result_get(t, copy=False)
+        chk = float(hv[-1]) + int(hc[-1])
+        ctx.vcm_result_release(t)
+        if i >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    del chk
+    e2e_total = reduce_max(float(sum(e2e_ms)), pg, dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_rate(scene, req, args.cpu_seconds)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+               "sample": "%d random viewpoints of the workload (%d patches each), %.1f s of CPU work"
+                         % (r["viewpoints"], P, r["seconds"])}
+
+    if rank == 0:
+        pk = peaks()
+        props = torch.cuda.get_device_properties(dev)
+        sm_count = props.multi_processor_count
+        max_mhz = float(pk.get("sm_max_mhz", 2070.0))
+        peak = alu_peak_ops(sm_count, max_mhz)
+        kern_avg_s = float(np.mean(kern_ms)) / 1e3
+        achieved = stats["slab_tests"] * OPS_PER_SLAB_TEST / kern_avg_s
+        value = world * seg * K / (total_ms / 1e3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": config_dict(scene, req),
+            "cells_per_s": world * n_vp * K / (total_ms / 1e3),
+            "kernel_ms": float(np.mean(kern_ms)),
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_tiles", "ops_per_unit": OPS_PER_SLAB_TEST,
+                         "units_per_launch": stats["slab_tests"],
+                         "peak_basis": "%d SMs x 128 lane-instr/clk x %.0f MHz (issue limit)" % (sm_count, max_mhz)},
+            "stats": {"slab_tests": stats["slab_tests"], "rechecked": stats["rechecked"],
+                      "boxes_listed": stats["boxes_listed"], "edge_cells": stats["edge_cells"],
+                      "v_ref": stats["v_ref"], "nonzero_cells": int((v > 0).sum().item())},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * seg * K / (e2e_total / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(lo.nbytes + hi.nbytes + 4 * len(req["layer_z"])),
+                    "d2h_bytes_per_step": int(n_vp * 5 + 48),
+                    "ms_per_step": e2e_total / K},
+            "gpu_launches": 3 * K,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched uneven requests (one persistent launch) and serving
+# ---------------------------------------------------------------------------
+
+def _alloc_outputs(torch, dev, reqs):
+    from paper_1310_7297_gb300 import n_viewpoints
+
+    vs = [torch.empty(n_viewpoints(r), dtype=torch.float32, device=dev) for r in reqs]
+    cs = [torch.empty(n_viewpoints(r), dtype=torch.uint8, device=dev) for r in reqs]
+    st = torch.empty(48 * len(reqs), dtype=torch.uint8, device=dev)
+    return vs, cs, st
+
+
+def run_batched(args):
+    """256 uneven requests over a shared 50,000-box scene: one persistent
+    launch (autotuned shapes) against one launch per request."""
+    import torch
+
+    import synth
+    from paper_1310_7297_gb300 import Context, n_viewpoints
+    from paper_1310_7297_gb300 import build as B
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    scene, reqs = synth.workload_batched(n_requests=args.batch_requests)
+    seg = sum(n_viewpoints(r) * r["patches_u"] * r["patches_w"] for r in reqs)
+    ctx = Context(0)
+    ctx.load_scene(scene)
+    ctx.vcm_build(50.0)
+    t0 = time.perf_counter()
+    samples = sorted(reqs, key=lambda r: n_viewpoints(r))[: max(4, len(reqs) // 16)]
+    tuned = ctx.vcm_autotune(samples)
+    tune_s = time.perf_counter() - t0
+    vs, cs, st = _alloc_outputs(torch, dev, reqs)
+    stream = torch.cuda.current_stream(dev)
+
+    def batch():
+        ctx.vcm_compute_batch(reqs, [t.data_ptr() for t in vs], [t.data_ptr() for t in cs], [None] * len(reqs),
+                              st.data_ptr(), stream.cuda_stream)
+
+    def singles():
+        for i, r in enumerate(reqs):
+            ctx.vcm_compute(r, vs[i].data_ptr(), cs[i].data_ptr(), None, st.data_ptr() + 48 * i, stream.cuda_stream)
+
+    res = {}
+    for name, fn in (("persistent_batch", batch), ("one_per_launch", singles)):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        res[name] = {"ms": float(np.median(ms)), "segments_per_s": seg / (float(np.median(ms)) / 1e3)}
+    print(json.dumps({"mode": "batched", "metric": METRIC, "unit": UNIT, "requests": len(reqs), "boxes": scene.n,
+                      "segments": seg, "autotune_s": tune_s, "tuned_shapes": sorted(set(map(tuple, tuned))),
+                      **res, "speedup": res["one_per_launch"]["ms"] / res["persistent_batch"]["ms"]}), flush=True)
+    ctx.close()
+
+
+def run_serve(args):
+    """Poisson arrivals of requests from the batched mix against a resident
+    100,000-box scene: continuous batching (vcm_submit/vcm_poll) against a
+    FIFO server that runs one request per launch."""
+    import torch
+
+    import synth
+    from paper_1310_7297_gb300 import Context, n_viewpoints
+    from paper_1310_7297_gb300 import build as B
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    scene, _ = synth.workload_3d_large(grid=64, layers=1)
+    ctx = Context(0, 64 << 30)
+    ctx.load_scene(scene)
+    ctx.vcm_build(50.0)
+    pool = synth.serving_requests(scene, count=args.serve_pool)
+    seg_of = [n_viewpoints(r) * r["patches_u"] * r["patches_w"] for r in pool]
+    stream = torch.cuda.current_stream(dev)
+    vs, cs, st = _alloc_outputs(torch, dev, pool)
+    # service time of each request alone, one launch each
+    for i, r in enumerate(pool[:4]):
+        ctx.vcm_compute(r, vs[i].data_ptr(), cs[i].data_ptr(), None, st.data_ptr() + 48 * i, stream.cuda_stream)
+    torch.cuda.synchronize()
+    service = []
+    for i, r in enumerate(pool):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.vcm_compute(r, vs[i].data_ptr(), cs[i].data_ptr(), None, st.data_ptr() + 48 * i, stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        service.append(a.elapsed_time(b))
+    del vs, cs, st
+    out = []
+    for rate in args.rates:
+        n = int(min(args.serve_count, max(40, rate * args.serve_seconds)))
+        arr = synth.poisson_arrivals(int(rate), float(rate), n)
+        picks = [pool[i % len(pool)] for i in range(n)]
+        seg = sum(seg_of[i % len(pool)] for i in range(n))
+        # FIFO, one request per launch: start = max(arrival, previous done)
+        done, lat = 0.0, []
+        for i in range(n):
+            start = max(arr[i], done)
+            done = start + service[i % len(pool)] / 1e3
+            lat.append(1e3 * (done - arr[i]))
+        fifo = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "segments_per_s": seg / done}
+        # continuous batching through the scheduler, in real time
+        tickets = [None] * n
+        t0 = time.perf_counter()
+        for i in range(n):
+            now = time.perf_counter() - t0
+            if arr[i] > now:
+                time.sleep(arr[i] - now)
+            tickets[i] = (ctx.vcm_submit(picks[i]), time.perf_counter() - t0)
+        lat2 = []
+        last = 0.0
+        for i, (t, ts) in enumerate(tickets):
+            ctx.vcm_poll(t, -1)
+            _, _, _, stt = ctx.vcm_result_get(t, copy=False)
+            # queueing from the arrival instant plus the library's submit-to-done time
+            lat2.append((ts - arr[i]) * 1e3 + stt["latency_ms"])
+            last = max(last, arr[i] + lat2[-1] / 1e3)
+            ctx.vcm_result_release(t)
+        cont = {"p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
+                "segments_per_s": seg / last}
+        out.append({"rate_per_s": rate, "requests": n, "continuous": cont, "one_per_launch_fifo": fifo})
+    print(json.dumps({"mode": "serve", "metric": METRIC, "unit": UNIT, "boxes": scene.n, "budget_gb": 64,
+                      "mean_service_ms": float(np.mean(service)), "rates": out}), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["step", "batched", "serve"], default="step",
+                    help="step: the timed VCM step (default); batched / serve: the batching and serving runs")
+    ap.add_argument("--batch-requests", type=int, default=256)
+    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-count", type=int, default=400)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--rates", type=float, nargs="+", default=[50, 100, 200, 500, 1000, 2000])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.mode == "batched":
+        run_batched(args)
+    elif args.mode == "serve":
+        run_serve(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

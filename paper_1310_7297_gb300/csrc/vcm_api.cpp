@@ -877,6 +877,7 @@ void scheduler_loop(vcm_ctx *ctx)
         }
         // admit groups from the front of the queue while memory allows
         std::vector<std::shared_ptr<Ticket>> batch;
+        bool alloc_failed = false;
         while (!ctx->queue.empty()) {
             auto &grp = ctx->queue.front();
             size_t need = 0;
@@ -898,6 +899,7 @@ void scheduler_loop(vcm_ctx *ctx)
             if (!ok) {
                 for (auto &t : grp)
                     release_buffers(ctx, *t);
+                alloc_failed = true;
                 break;
             }
             for (auto &t : grp)
@@ -905,8 +907,10 @@ void scheduler_loop(vcm_ctx *ctx)
             ctx->queue.pop_front();
         }
         if (batch.empty()) {
-            // the head does not fit while other work holds memory: wait
-            if (ctx->running_groups == 0) {
+            // The head does not fit the budget: finished results still hold
+            // memory until released, so wait.  Only a device allocation that
+            // fails with nothing in flight is final.
+            if (alloc_failed && ctx->running_groups == 0) {
                 auto grp = ctx->queue.front();
                 ctx->queue.pop_front();
                 for (auto &t : grp) {

@@ -156,6 +156,9 @@ __global__ void k_cell_bounds(const float4 *__restrict__ boxes, const int *__res
 // tile kernel
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ float4 world_box_lo(const DevScene &sc, int s) { return __ldg(&sc.boxes[0][2 * s]); }
+__device__ __forceinline__ float4 world_box_hi(const DevScene &sc, int s) { return __ldg(&sc.boxes[0][2 * s + 1]); }
+
 struct __align__(16) Plane {
     float x, y, z, c;
 };
@@ -393,7 +396,6 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                     lo = __ldg(&gbox[2 * s]);
                     hi = __ldg(&gbox[2 * s + 1]);
                 }
-                ++nb;
                 const float a_u = lo.x - qu, b_u = hi.x - qu;
                 const float a_n = lo.y - qn, b_n = hi.y - qn;
                 const float a_w = lo.z - qw, b_w = hi.z - qw;
@@ -406,6 +408,7 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                 // no row of this column can meet the box: skip the rows
                 if (__all_sync(kFull, alive == 0 || (pre_x - pre_e) < -kBand))
                     continue;
+                ++nb;   // boxes whose rows are tested
                 const float near_w = sgn_w_uni ? a_w : b_w;
                 const float far_w = sgn_w_uni ? b_w : a_w;
 #pragma unroll
@@ -628,6 +631,47 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         const int count = sm.count;
         const int n_smem = min(count, box_cap);
         const float4 *gbox = sc.boxes[R.perm];
+        // near-first order of the staged candidates: nearby boxes block the
+        // most sightlines, so the all-blocked exit comes early.  Keys are the
+        // squared footprint distance from the tile centre (a positive float,
+        // so its bits order like the value) above the sorted box index.
+        if (n_smem > 1) {
+            unsigned long long *keyed = reinterpret_cast<unsigned long long *>(s_box);
+            int N = 1;
+            while (N < n_smem)
+                N <<= 1;
+            const float cx = 0.5f * (R.x_coord[ix0] + R.x_coord[ix1 - 1]);
+            const float cy = 0.5f * (R.y_coord[iy0] + R.y_coord[iy1 - 1]);
+            for (int i = tid; i < N; i += kThreads) {
+                unsigned long long k = ~0ull;
+                if (i < n_smem) {
+                    const int s = s_ids[i];
+                    const float4 l = world_box_lo(sc, s), h = world_box_hi(sc, s);
+                    const float dx = 0.5f * (l.x + h.x) - cx, dy = 0.5f * (l.y + h.y) - cy;
+                    k = ((unsigned long long)__float_as_uint(fmaf(dx, dx, dy * dy)) << 32) | (unsigned)s;
+                }
+                keyed[i] = k;
+            }
+            __syncthreads();
+            for (int k = 2; k <= N; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int i = tid; i < N; i += kThreads) {
+                        const int p = i ^ j;
+                        if (p > i) {
+                            const unsigned long long a = keyed[i], b = keyed[p];
+                            if ((a > b) == ((i & k) == 0)) {
+                                keyed[i] = b;
+                                keyed[p] = a;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int i = tid; i < n_smem; i += kThreads)
+                s_ids[i] = (int)(keyed[i] & 0xffffffffu);
+            __syncthreads();
+        }
         for (int i = tid; i < n_smem; i += kThreads) {
             const float4 *src = gbox + 2 * s_ids[i];
             cp_async16(&s_box[2 * i], src);
@@ -728,9 +772,8 @@ __global__ void k_quantise(const DevRequest *__restrict__ reqs, const long long 
         }
         if (R.color_out)
             R.color_out[local] = c;
-        const unsigned ballot = __ballot_sync(__activemask(), edge);
-        if (edge && (threadIdx.x & 31) == (unsigned)(__ffs(ballot) - 1))
-            atomicAdd(&R.stats->edge_cells, (unsigned)__popc(ballot));
+        if (edge)   // rare; lanes of one warp may belong to different requests
+            atomicAdd(&R.stats->edge_cells, 1u);
         if (local == 0)
             R.stats->v_ref = vref;
     }

@@ -1,0 +1,96 @@
+"""Continuous batching through vcm_submit / vcm_poll (GPU).
+
+Requests submitted together are merged by the scheduler into batched
+launches on several slots; each result must be the same as the request run
+alone (bit for bit: per-viewpoint sums do not depend on batching).  Memory
+admission holds requests back until the budget frees up, over-budget
+requests are refused, and queued requests can be cancelled.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scene_reqs():
+    return synth.workload_batched(seed=13, n_requests=16, n_boxes=4000, min_side=3, max_side=7)
+
+
+def _ctx(scene, budget=0):
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1310_7297_gb300 import Context
+
+    c = Context(0, budget)
+    c.load_scene(scene)
+    c.vcm_build(50.0)
+    return c
+
+
+def test_mix_equals_alone(scene_reqs):
+    scene, reqs = scene_reqs
+    ctx = _ctx(scene)
+    try:
+        alone = [gpu_run(ctx, dict(r, flags=1), bits=True) for r in reqs]
+        ctx.vcm_set_slots(3, 5)
+        tickets = [ctx.vcm_submit(dict(r, flags=1)) for r in reqs]
+        tickets += ctx.vcm_submit_batch([dict(r, flags=1) for r in reqs[:4]])
+        for i, t in enumerate(tickets):
+            assert ctx.vcm_poll(t, -1) == 0
+            v, c, b, st = ctx.vcm_result_get(t)
+            ref = alone[i % len(reqs)]
+            assert np.array_equal(v.astype(np.float64), ref[0]), i
+            assert np.array_equal(c, ref[1]), i
+            assert np.array_equal(b, ref[2]), i
+            ctx.vcm_result_release(t)
+    finally:
+        ctx.close()
+
+
+def test_memory_admission_and_rejection(scene_reqs):
+    from paper_1310_7297_gb300 import VcmError, n_viewpoints
+
+    scene, reqs = scene_reqs
+    biggest = max(n_viewpoints(r) * 5 for r in reqs)
+    ctx = _ctx(scene, budget=biggest + 4096)   # room for about one request at a time
+    try:
+        tickets = [ctx.vcm_submit(r) for r in reqs[:8]]
+        for t in tickets:
+            assert ctx.vcm_poll(t, -1) == 0
+            ctx.vcm_result_release(t)
+        r_big = max(reqs, key=n_viewpoints)
+        huge = dict(r_big, layer_z=[1741] * 4096)   # 4096 layers: far beyond the budget
+        with pytest.raises(VcmError) as e:
+            ctx.vcm_submit(huge)
+        assert e.value.status == -3   # VCM_E_NOMEM
+    finally:
+        ctx.close()
+
+
+def test_cancel_queued_request(scene_reqs):
+    from paper_1310_7297_gb300 import VcmError
+
+    scene, reqs = scene_reqs
+    ctx = _ctx(scene)
+    try:
+        ctx.vcm_set_slots(1, 1)
+        big = dict(reqs[0], layer_z=[1741 + 10240 * (k % 8) for k in range(64)])
+        tickets = [ctx.vcm_submit(big) for _ in range(3)] + [ctx.vcm_submit(reqs[1])]
+        ctx.vcm_cancel(tickets[-1])
+        with pytest.raises(VcmError) as e:
+            ctx.vcm_poll(tickets[-1], 0)
+        assert e.value.status == -6   # VCM_E_CANCELLED
+        for t in tickets[:-1]:
+            assert ctx.vcm_poll(t, -1) == 0
+            with pytest.raises(VcmError):
+                ctx.vcm_cancel(t)     # already admitted / finished
+            ctx.vcm_result_release(t)
+        ctx.vcm_result_release(tickets[-1])
+    finally:
+        ctx.close()
