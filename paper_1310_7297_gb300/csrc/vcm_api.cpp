@@ -26,6 +26,8 @@
 
 using namespace vcm;
 
+struct Ticket;   // one asynchronous request (defined below)
+
 namespace {
 
 thread_local std::string t_err;
@@ -353,6 +355,12 @@ struct Slot {
     vcm_stats *d_stats = nullptr;
     size_t stats_cap = 0;   // entries
     bool busy = false;
+    // completion: the slot's waiter thread blocks on `done` (without any
+    // lock held), then marks the in-flight group finished
+    cudaEvent_t done = nullptr;
+    std::vector<std::shared_ptr<::Ticket>> inflight;
+    bool posted = false;
+    std::thread waiter;
     // graph of the device work of one batched launch
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -370,8 +378,6 @@ struct Layout {
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
-
-struct Ticket;
 
 struct vcm_ctx {
     int device = 0;
@@ -734,30 +740,45 @@ bool scheduler_idle(vcm_ctx *ctx) { return ctx->queue.empty() && ctx->running_gr
 // scheduler
 // ---------------------------------------------------------------------------
 
-struct Done {
-    vcm_ctx *ctx;
-    std::vector<std::shared_ptr<Ticket>> group;
-    Slot *slot;
-};
-
-void CUDART_CB on_group_done(void *arg)
+// Completion of a slot's launches.  CUDA host callbacks are not used: a
+// callback that takes the context lock can deadlock against a thread that
+// holds the lock inside a call that implicitly synchronises the device
+// (cudaMallocHost, cudaFree).  This thread waits on the slot's event with no
+// lock held and only then takes the lock.
+void slot_waiter(vcm_ctx *ctx, Slot *s)
 {
-    Done *d = static_cast<Done *>(arg);
-    {
-        std::lock_guard<std::mutex> g(d->ctx->mu);
+    cudaSetDevice(ctx->device);
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    for (;;) {
+        ctx->cv.wait(lk, [&] { return s->posted || ctx->stop; });
+        if (!s->posted)
+            return;   // stopping with nothing in flight
+        std::vector<std::shared_ptr<Ticket>> group;
+        group.swap(s->inflight);
+        s->posted = false;
+        cudaEvent_t ev = s->done;
+        lk.unlock();
+        const cudaError_t e = cudaEventSynchronize(ev);
+        lk.lock();
         const auto now = std::chrono::steady_clock::now();
-        for (auto &t : d->group) {
-            if (t->h_stats && t->h_stats->error)
-                t->state = T_ERROR, t->err = VCM_E_CUDA, t->msg = "device-side check failed";
-            else
+        for (auto &t : group) {
+            if (e != cudaSuccess) {
+                t->state = T_ERROR;
+                t->err = VCM_E_CUDA;
+                t->msg = std::string("launch failed: ") + cudaGetErrorString(e);
+            } else if (t->h_stats && t->h_stats->error) {
+                t->state = T_ERROR;
+                t->err = VCM_E_CUDA;
+                t->msg = "device-side check failed";
+            } else {
                 t->state = T_DONE;
+            }
             t->t_done = now;
         }
-        d->slot->busy = false;
-        d->ctx->running_groups--;
+        s->busy = false;
+        ctx->running_groups--;
+        ctx->cv.notify_all();
     }
-    d->ctx->cv.notify_all();
-    delete d;
 }
 
 void release_buffers(vcm_ctx *ctx, Ticket &t)
@@ -838,18 +859,18 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
                                 s.stream);
             cudaMemcpyAsync(t.h_stats, s.d_stats + i, sizeof(vcm_stats), cudaMemcpyDeviceToHost, s.stream);
         }
-        Done *d = new Done{ctx, group, &s};
-        if (cudaLaunchHostFunc(s.stream, on_group_done, d) == cudaSuccess) {
+        if (cudaEventRecord(s.done, s.stream) == cudaSuccess) {
             for (auto &t : group) {
                 t->state = T_RUNNING;
                 t->slot = &s;
             }
+            s.inflight = group;
+            s.posted = true;
             s.busy = true;
             ctx->running_groups++;
             return;
         }
-        delete d;
-        st = fail(VCM_E_CUDA, "cudaLaunchHostFunc failed");
+        st = fail(VCM_E_CUDA, "cudaEventRecord failed");
     }
     for (auto &t : group) {
         t->state = T_ERROR;
@@ -936,9 +957,12 @@ vcm_status start_scheduler(vcm_ctx *ctx, uint32_t n_slots)
         auto s = std::make_unique<Slot>();
         CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
         CUDA_TRY(cudaEventCreateWithFlags(&s->desc_copied, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
         ctx->slots.push_back(std::move(s));
     }
     ctx->stop = false;
+    for (auto &s : ctx->slots)
+        s->waiter = std::thread(slot_waiter, ctx, s.get());
     ctx->worker = std::thread(scheduler_loop, ctx);
     return VCM_OK;
 }
@@ -953,6 +977,8 @@ void stop_scheduler(vcm_ctx *ctx)
     if (ctx->worker.joinable())
         ctx->worker.join();
     for (auto &s : ctx->slots) {
+        if (s->waiter.joinable())
+            s->waiter.join();   // finishes any posted group first
         if (s->stream)
             cudaStreamSynchronize(s->stream);
     }
@@ -968,8 +994,20 @@ void destroy_slot(Slot &s)
     if (s.d_spill) cudaFree(s.d_spill);
     if (s.d_stats) cudaFree(s.d_stats);
     if (s.desc_copied) cudaEventDestroy(s.desc_copied);
+    if (s.done) cudaEventDestroy(s.done);
     if (s.stream) cudaStreamDestroy(s.stream);
-    s = Slot{};
+    s.inflight.clear();
+    s.stream = nullptr;
+    s.desc_copied = s.done = nullptr;
+    s.d_desc = s.h_desc = nullptr;
+    s.desc_cap = 0;
+    s.d_work = s.d_spill = nullptr;
+    s.spill_cap = 0;
+    s.d_stats = nullptr;
+    s.stats_cap = 0;
+    s.busy = s.posted = false;
+    s.graph = nullptr;
+    s.exec = nullptr;
 }
 
 vcm_status validate_ctx(vcm_ctx *ctx)
