@@ -249,6 +249,8 @@ def run_gpu(args):
     e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     kb = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ka = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for e in kb + ka:
+        e.record(stream)   # torch creates the CUDA event on first record; the library re-records it
     torch.cuda.synchronize()
     for i in range(K):
         flush.zero_()

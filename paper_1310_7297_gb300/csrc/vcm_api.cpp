@@ -632,10 +632,13 @@ vcm_status prepare_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *
 // kernel and the quantiser, in stream order.  The node sequence is the same
 // for every launch, so a captured graph can be updated in place.
 vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *stats, cudaStream_t stream,
-                         bool timed = false)
+                         bool timed = false, bool capturing = false)
 {
     CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, P.L.bytes, cudaMemcpyHostToDevice, stream));
-    CUDA_TRY(cudaEventRecord(s.desc_copied, stream));
+    // An event recorded inside a stream capture cannot be waited on later;
+    // a captured launch records it after the graph launch instead.
+    if (!capturing)
+        CUDA_TRY(cudaEventRecord(s.desc_copied, stream));
     CUDA_TRY(cudaMemsetAsync(s.d_work, 0, sizeof(int), stream));
     CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(vcm_stats) * P.n, stream));
     const DevRequest *d_reqs = reinterpret_cast<const DevRequest *>(s.d_desc + P.L.off_reqs);
@@ -674,7 +677,7 @@ vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *>
     if (st != VCM_OK)
         return st;
     CUDA_TRY(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeRelaxed));
-    st = record_launch(ctx, s, P, stats, s.stream);
+    st = record_launch(ctx, s, P, stats, s.stream, false, true);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s.stream, &g);
     if (st != VCM_OK) {
@@ -704,6 +707,7 @@ vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *>
         cudaGraphDestroy(s.graph);
     s.graph = g;
     CUDA_TRY(cudaGraphLaunch(s.exec, s.stream));
+    CUDA_TRY(cudaEventRecord(s.desc_copied, s.stream));
     return VCM_OK;
 }
 
