@@ -235,6 +235,39 @@ vcm_status vcm_set_tune(vcm_ctx *ctx, const vcm_tune *tune);
 /* Launch shape the context would use for this request. */
 vcm_status vcm_get_tune(vcm_ctx *ctx, const vcm_request *req, vcm_tune *out);
 
+/* ---- without device allocation ----------------------------------------- */
+
+#define VCM_STATIC_MAX_BOXES 4096u
+#define VCM_STATIC_MAX_COORDS 65536u   /* patches_u + patches_w + grid_nx + grid_ny + n_layers */
+#define VCM_STATIC_SCRATCH_BYTES (8u << 20)
+
+/* One request computed without allocating any device memory, for callers
+ * that must not call cudaMalloc: code running under an allocator that owns
+ * all device memory (a framework's caching pool, a fixed memory budget), or
+ * a plug-in that may not change the process's device footprint while it
+ * runs.  The paper has no counterpart; this is an interface convenience.
+ *
+ * Inputs: the obstacle boxes as host arrays lo/hi of n_boxes x dims floats
+ * (same rules as vcm_scene_load_mem) and the request.  Outputs: caller-owned
+ * device buffers with the meaning of vcm_compute (d_v, d_color or NULL,
+ * d_bits iff VCM_EMIT_BITS, d_stats).  No context is needed.  The index,
+ * descriptors and counters live in one file-scope device array of
+ * VCM_STATIC_SCRATCH_BYTES, which every GPU that loads libvcm holds until
+ * the process exits.  Requests beyond VCM_STATIC_MAX_BOXES boxes or
+ * VCM_STATIC_MAX_COORDS coordinates are rejected with VCM_E_ARG.
+ *
+ * The work is enqueued on `stream` (a cudaStream_t, NULL = legacy default)
+ * of the current device; host inputs are consumed before the call returns.
+ * The first call on a device looks up the array's device address and
+ * uploads constant tables; make that first call before any stream capture.
+ * Every call on a device reuses that device's array and leaves the last
+ * call's contents in it (each call clears what must start at zero).  Calls
+ * whose work overlaps on the same GPU, e.g. on two streams, race on the
+ * array: serialise them, for instance by issuing them on one stream. */
+vcm_status vcm_compute_static(const float *lo, const float *hi, uint32_t n_boxes, int32_t dims,
+                              const vcm_request *req, float *d_v, uint8_t *d_color, uint32_t *d_bits,
+                              vcm_stats *d_stats, void *stream);
+
 /* ---- profiling --------------------------------------------------------- */
 
 /* Record two caller-created CUDA events (cudaEvent_t) on the launch stream

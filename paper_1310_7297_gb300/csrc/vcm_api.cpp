@@ -1517,6 +1517,148 @@ vcm_status vcm_get_tune(vcm_ctx *ctx, const vcm_request *req, vcm_tune *out)
     return VCM_OK;
 }
 
+vcm_status vcm_compute_static(const float *lo, const float *hi, uint32_t n_boxes, int32_t dims,
+                              const vcm_request *req, float *d_v, uint8_t *d_color, uint32_t *d_bits,
+                              vcm_stats *d_stats, void *stream)
+{
+    try {
+        if (dims != 2 && dims != 3)
+            return fail(VCM_E_ARG, "dims must be 2 or 3");
+        if (n_boxes > VCM_STATIC_MAX_BOXES)
+            return fail(VCM_E_ARG, "vcm_compute_static takes at most %u boxes (got %u)", VCM_STATIC_MAX_BOXES,
+                        n_boxes);
+        if (n_boxes > 0 && (!lo || !hi))
+            return fail(VCM_E_ARG, "lo/hi are NULL");
+        if (!d_v || !d_stats)
+            return fail(VCM_E_ARG, "d_v and d_stats are required");
+        Canon c;
+        vcm_status st = canonicalise(req, c);
+        if (st != VCM_OK)
+            return st;
+        if (c.dims != dims)
+            return fail(VCM_E_ARG, "request dims %d differ from the boxes' dims %d", c.dims, dims);
+        if ((c.flags & VCM_EMIT_BITS) && !d_bits)
+            return fail(VCM_E_ARG, "VCM_EMIT_BITS needs d_bits");
+        if ((unsigned)c.coord_count() > VCM_STATIC_MAX_COORDS)
+            return fail(VCM_E_ARG, "vcm_compute_static takes at most %u coordinates (patches_u + patches_w + "
+                        "grid_nx + grid_ny + n_layers = %d)", VCM_STATIC_MAX_COORDS, c.coord_count());
+        // boxes: lattice checks, world copy n x 3, bounds and largest extent
+        const uint32_t n = n_boxes;
+        std::vector<float> L((size_t)std::max<uint32_t>(n, 1) * 3, 0.f), H(L.size(), 0.f);
+        double x0 = 0, x1 = 1, y0 = 0, y1 = 1, ext = 0;
+        if (n) {
+            x0 = y0 = 1e30;
+            x1 = y1 = -1e30;
+        }
+        for (uint32_t i = 0; i < n; ++i) {
+            for (int k = 0; k < dims; ++k) {
+                const float a = lo[(size_t)i * dims + k], b = hi[(size_t)i * dims + k];
+                int64_t ua, ub;
+                if (!to_units(a, ua) || !to_units(b, ub))
+                    return fail(VCM_E_ARG, "box %u coordinate %d is not a finite lattice value within 16384 m", i, k);
+                if (ua > ub)
+                    return fail(VCM_E_ARG, "box %u has lo > hi on axis %d", i, k);
+                L[(size_t)i * 3 + k] = a;
+                H[(size_t)i * 3 + k] = b;
+            }
+            x0 = std::min<double>(x0, L[3 * i]);
+            x1 = std::max<double>(x1, H[3 * i]);
+            y0 = std::min<double>(y0, L[3 * i + 1]);
+            y1 = std::max<double>(y1, H[3 * i + 1]);
+            ext = std::max<double>(ext, std::max(H[3 * i] - L[3 * i], H[3 * i + 1] - L[3 * i + 1]));
+        }
+        const double w = std::max(x1 - x0, 1.0), h = std::max(y1 - y0, 1.0);
+        double cell = std::max(std::sqrt(w * h / std::max<uint32_t>(n, 1)) * 1.5, 1.0);
+        const double max_cells = 65536.0;
+        while ((std::ceil(w / cell) + 1) * (std::ceil(h / cell) + 1) > max_cells)
+            cell *= 1.25;
+        const int gnx = (int)std::ceil(w / cell) + 1, gny = (int)std::ceil(h / cell) + 1;
+        const int n_cells = gnx * gny;
+
+        // place everything in the static scratch array
+        CUDA_TRY(init_device());
+        void *base = nullptr;
+        size_t cap = 0;
+        CUDA_TRY(static_scratch(&base, &cap));
+        const size_t nb = std::max<uint32_t>(n, 1);
+        vcm_tune t = default_tune();
+        t.box_cap = (uint32_t)std::max<size_t>(32, nb);   // every candidate list fits: no spill
+        std::vector<const Canon *> cs{&c};
+        std::vector<vcm_tune> shapes{t};
+        const Layout lay = layout_for(cs, shapes);
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            const size_t at = off;
+            off = align_up(off + bytes, 256);
+            return static_cast<char *>(base) + at;
+        };
+        float *s_lo = reinterpret_cast<float *>(take(nb * 3 * sizeof(float)));
+        float *s_hi = reinterpret_cast<float *>(take(nb * 3 * sizeof(float)));
+        float4 *s_perm[6];
+        for (auto &p : s_perm)
+            p = reinterpret_cast<float4 *>(take(nb * 2 * sizeof(float4)));
+        int *s_cell_of = reinterpret_cast<int *>(take(nb * sizeof(int)));
+        int *s_order = reinterpret_cast<int *>(take(nb * sizeof(int)));
+        int *s_count = reinterpret_cast<int *>(take((size_t)n_cells * sizeof(int)));
+        int *s_cursor = reinterpret_cast<int *>(take((size_t)n_cells * sizeof(int)));
+        int *s_start = reinterpret_cast<int *>(take((size_t)(n_cells + 1) * sizeof(int)));
+        float4 *s_cell_lo = reinterpret_cast<float4 *>(take((size_t)n_cells * sizeof(float4)));
+        float4 *s_cell_hi = reinterpret_cast<float4 *>(take((size_t)n_cells * sizeof(float4)));
+        unsigned *s_overhang = reinterpret_cast<unsigned *>(take(sizeof(unsigned)));
+        int *s_work = reinterpret_cast<int *>(take(sizeof(int)));
+        int *s_spill = reinterpret_cast<int *>(take(256));   // never written: lists fit box_cap
+        char *s_desc = take(lay.bytes);
+        if (off > cap)
+            return fail(VCM_E_ARG, "request needs %zu bytes of static scratch, the array has %zu", off, cap);
+
+        cudaStream_t sm = static_cast<cudaStream_t>(stream);
+        // pageable host sources: each copy has consumed its source when it returns
+        CUDA_TRY(cudaMemcpyAsync(s_lo, L.data(), nb * 3 * sizeof(float), cudaMemcpyHostToDevice, sm));
+        CUDA_TRY(cudaMemcpyAsync(s_hi, H.data(), nb * 3 * sizeof(float), cudaMemcpyHostToDevice, sm));
+        CUDA_TRY(launch_grid_build(s_lo, s_hi, (int)n, dims, (float)x0, (float)y0, (float)cell, gnx, gny, s_cell_of,
+                                   s_count, s_cursor, s_order, s_start, s_perm, s_cell_lo, s_cell_hi, s_overhang, sm));
+        DevScene sc{};
+        for (int p = 0; p < 6; ++p)
+            sc.boxes[p] = s_perm[p];
+        sc.n_boxes = (int)n;
+        sc.dims = dims;
+        sc.cell_start = s_start;
+        sc.cell_lo = s_cell_lo;
+        sc.cell_hi = s_cell_hi;
+        sc.gx0 = (float)x0;
+        sc.gy0 = (float)y0;
+        sc.cell = (float)cell;
+        sc.inv_cell = (float)(1.0 / cell);
+        sc.gnx = gnx;
+        sc.gny = gny;
+        // A box is bucketed by its centre, so it reaches at most half its
+        // extent past its cell; the host bound avoids reading the device one.
+        sc.overhang = (float)(0.5 * ext + 1.0);
+
+        std::vector<char> hdesc(lay.bytes);
+        float *vv[1] = {d_v};
+        uint8_t *cc[1] = {d_color};
+        uint32_t *bb[1] = {d_bits};
+        fill_desc(hdesc.data(), s_desc, lay, cs, shapes, vv, cc, bb, d_stats, (int)t.box_cap);
+        CUDA_TRY(cudaMemcpyAsync(s_desc, hdesc.data(), lay.bytes, cudaMemcpyHostToDevice, sm));
+        CUDA_TRY(cudaMemsetAsync(s_work, 0, sizeof(int), sm));
+        CUDA_TRY(cudaMemsetAsync(d_stats, 0, sizeof(vcm_stats), sm));
+        const DevRequest *d_reqs = reinterpret_cast<const DevRequest *>(s_desc + lay.off_reqs);
+        const int *d_tiles = reinterpret_cast<const int *>(s_desc + lay.off_tiles);
+        const long long *d_vps = reinterpret_cast<const long long *>(s_desc + lay.off_vps);
+        int sm_count = 1, dev = 0;
+        CUDA_TRY(cudaGetDevice(&dev));
+        CUDA_TRY(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
+        const int blocks = std::max(1, std::min(lay.total_tiles, tiles_blocks_per_sm((int)t.box_cap, 16) * sm_count));
+        CUDA_TRY(launch_zero_bits(d_reqs, 1, sm));
+        CUDA_TRY(launch_tiles(sc, d_reqs, d_tiles, 1, lay.total_tiles, s_work, s_spill, blocks, (int)t.box_cap, 16, sm));
+        CUDA_TRY(launch_quantise(d_reqs, d_vps, 1, lay.total_vp, sm));
+        return VCM_OK;
+    } catch (const std::exception &ex) {
+        return fail(VCM_E_NOMEM, "vcm_compute_static: %s", ex.what());
+    }
+}
+
 vcm_status vcm_set_timing_events(vcm_ctx *ctx, void *before_tiles, void *after_tiles)
 {
     if (!ctx)

@@ -95,4 +95,8 @@ int tiles_blocks_per_sm(int box_cap, int k_rows_max);
 // before any launch is captured into a graph.
 cudaError_t init_device();
 
+// Device address and size of the file-scope scratch array used by
+// vcm_compute_static on the current device (looked up once per device).
+cudaError_t static_scratch(void **ptr, size_t *bytes);
+
 }  // namespace vcm

@@ -15,6 +15,7 @@
 
 #include <cfloat>
 #include <cstdio>
+#include <mutex>
 
 namespace vcm {
 
@@ -811,6 +812,34 @@ cudaError_t init_device()
         return e;
     if (dev >= 0 && dev < 64)
         done[dev] = true;
+    return cudaSuccess;
+}
+
+// Scratch for callers that cannot allocate device memory (vcm_compute_static).
+// A file-scope __device__ array: every GPU that loads the library holds it
+// until the process exits.  Host code must not use the symbol as a pointer;
+// it asks the runtime for the array's device address once per device.
+static __device__ __align__(256) unsigned char g_static_scratch[VCM_STATIC_SCRATCH_BYTES];
+
+cudaError_t static_scratch(void **ptr, size_t *bytes)
+{
+    static std::mutex mu;
+    static void *addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= 64)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if ((e = cudaGetSymbolAddress(&p, g_static_scratch)) != cudaSuccess)
+            return e;
+        addr[dev] = p;
+    }
+    *ptr = addr[dev];
+    *bytes = sizeof(g_static_scratch);
     return cudaSuccess;
 }
 

@@ -27,7 +27,7 @@ UNITS_PER_M = 1024
 EXPORTS = ["vcm_ctx_create", "vcm_ctx_destroy", "vcm_last_error", "vcm_scene_load_mem", "vcm_scene_load",
            "vcm_scene_save", "vcm_build", "vcm_compute", "vcm_submit", "vcm_submit_batch", "vcm_poll",
            "vcm_result_get", "vcm_result_release", "vcm_cancel", "vcm_set_slots", "vcm_compute_batch",
-           "vcm_autotune", "vcm_set_tune", "vcm_get_tune", "vcm_set_timing_events"]
+           "vcm_autotune", "vcm_set_tune", "vcm_get_tune", "vcm_set_timing_events", "vcm_compute_static"]
 
 
 class VcmError(RuntimeError):
@@ -100,6 +100,8 @@ def lib():
         L.vcm_set_tune.argtypes = [VP, P(vcm_tune)]
         L.vcm_get_tune.argtypes = [VP, P(vcm_request), P(vcm_tune)]
         L.vcm_set_timing_events.argtypes = [VP, VP, VP]
+        L.vcm_compute_static.argtypes = [P(ctypes.c_float), P(ctypes.c_float), ctypes.c_uint32, ctypes.c_int32,
+                                         P(vcm_request), VP, VP, VP, VP, VP]
         for name in EXPORTS:
             if name not in ("vcm_ctx_destroy", "vcm_last_error"):
                 getattr(L, name).restype = S
@@ -315,6 +317,19 @@ class Context:
         t = vcm_tune()
         self._ck(self.L.vcm_get_tune(self.h, ctypes.byref(r), ctypes.byref(t)))
         return (t.tile_x, t.tile_y, t.patch_k, t.box_cap)
+
+
+def vcm_compute_static(lo, hi, dims, req, d_v, d_color, d_bits, d_stats, stream):
+    """Module-level wrapper of the C entry point that allocates no device
+    memory (no context): host boxes lo/hi (n x dims), device outputs."""
+    lo = np.ascontiguousarray(np.asarray(lo, np.float32)[:, :dims])
+    hi = np.ascontiguousarray(np.asarray(hi, np.float32)[:, :dims])
+    r, keep = make_request(req)
+    fp = ctypes.POINTER(ctypes.c_float)
+    st = lib().vcm_compute_static(lo.ctypes.data_as(fp), hi.ctypes.data_as(fp), lo.shape[0], dims, ctypes.byref(r),
+                                  d_v, d_color, d_bits, d_stats, stream)
+    del keep
+    return _check(st)
 
 
 def stats_from_tensor(s):
