@@ -31,10 +31,13 @@ if ROOT not in sys.path:
 METRIC = "viewpoint-patch occlusion tests/sec and VCM cells/sec at ≤1e-5 rel err; p50/p99 latency"
 UNIT = "segments/s"
 WORKLOAD = "3D plain VCM: 512x512 viewpoints x 5 layers, 5,000 mixture boxes over 2 km, 20x10 m target, 32x16 patches"
-# Lane-level operations of one separable slab test in the row loop of the
-# tile kernel: 2 FMUL (w interval), 3 FMNMX (enter/exit), 1 FADD (margin),
-# 1 FSETP (band compare).
-OPS_PER_SLAB_TEST = 7
+# Lane-level operations the tile kernel issues per segment/box slab test:
+# a row test of the sweep is 2 FMUL (w interval), 3 FMNMX (entry/exit),
+# 1 FADD (margin), 1 FSETP (band compare); a corner test of the
+# one-box-blocks-all check is a quarter of its ~60 operations per box
+# (5 reciprocals, 6 FADD, 10 SEL, 10 FMUL, 4 x (4 FMNMX, FADD, FSETP)).
+OPS_PER_ROW_TEST = 7
+OPS_PER_CORNER_TEST = 15
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -202,6 +205,7 @@ def run_gpu(args):
     import synth
     from paper_1310_7297_gb300 import Context, stats_from_tensor
     from paper_1310_7297_gb300 import build as B
+    from paper_1310_7297_gb300.vcm import STATS_BYTES
 
     world, rank, local = dist_setup()
     B.build()
@@ -223,7 +227,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     v = torch.empty(n_vp, dtype=torch.float32, device=dev)
     col = torch.empty(n_vp, dtype=torch.uint8, device=dev)
-    st = torch.empty(48, dtype=torch.uint8, device=dev)
+    st = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -301,7 +305,8 @@ def run_gpu(args):
         max_mhz = float(pk.get("sm_max_mhz", 2070.0))
         peak = alu_peak_ops(sm_count, max_mhz)
         kern_avg_s = float(np.mean(kern_ms)) / 1e3
-        achieved = stats["slab_tests"] * OPS_PER_SLAB_TEST / kern_avg_s
+        units = stats["slab_tests"] + stats["corner_tests"]
+        achieved = (stats["slab_tests"] * OPS_PER_ROW_TEST + stats["corner_tests"] * OPS_PER_CORNER_TEST) / kern_avg_s
         value = world * seg * K / (total_ms / 1e3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -312,16 +317,18 @@ def run_gpu(args):
             "kernel_ms": float(np.mean(kern_ms)),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_tiles", "ops_per_unit": OPS_PER_SLAB_TEST,
-                         "units_per_launch": stats["slab_tests"],
+                         "kernel": "k_tiles", "work_unit": "segment/box slab test",
+                         "ops_per_unit": {"row_test": OPS_PER_ROW_TEST, "corner_test": OPS_PER_CORNER_TEST},
+                         "units_per_launch": units,
                          "peak_basis": "%d SMs x 128 lane-instr/clk x %.0f MHz (issue limit)" % (sm_count, max_mhz)},
-            "stats": {"slab_tests": stats["slab_tests"], "rechecked": stats["rechecked"],
+            "stats": {"slab_tests": stats["slab_tests"], "corner_tests": stats["corner_tests"],
+                      "shortcut_viewpoints": stats["shortcut_viewpoints"], "rechecked": stats["rechecked"],
                       "boxes_listed": stats["boxes_listed"], "edge_cells": stats["edge_cells"],
                       "v_ref": stats["v_ref"], "nonzero_cells": int((v > 0).sum().item())},
             "cpu_baseline": cpu,
             "e2e": {"value": world * seg * K / (e2e_total / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": int(lo.nbytes + hi.nbytes + 4 * len(req["layer_z"])),
-                    "d2h_bytes_per_step": int(n_vp * 5 + 48),
+                    "d2h_bytes_per_step": int(n_vp * 5 + STATS_BYTES),
                     "ms_per_step": e2e_total / K},
             "gpu_launches": 3 * K,
             "clocks": clocks,
@@ -338,10 +345,11 @@ def run_gpu(args):
 
 def _alloc_outputs(torch, dev, reqs):
     from paper_1310_7297_gb300 import n_viewpoints
+    from paper_1310_7297_gb300.vcm import STATS_BYTES
 
     vs = [torch.empty(n_viewpoints(r), dtype=torch.float32, device=dev) for r in reqs]
     cs = [torch.empty(n_viewpoints(r), dtype=torch.uint8, device=dev) for r in reqs]
-    st = torch.empty(48 * len(reqs), dtype=torch.uint8, device=dev)
+    st = torch.empty(STATS_BYTES * len(reqs), dtype=torch.uint8, device=dev)
     return vs, cs, st
 
 
@@ -353,6 +361,7 @@ def run_batched(args):
     import synth
     from paper_1310_7297_gb300 import Context, n_viewpoints
     from paper_1310_7297_gb300 import build as B
+    from paper_1310_7297_gb300.vcm import STATS_BYTES
 
     B.build()
     dev = torch.device("cuda", 0)
@@ -374,7 +383,7 @@ def run_batched(args):
 
     def singles():
         for i, r in enumerate(reqs):
-            ctx.vcm_compute(r, vs[i].data_ptr(), cs[i].data_ptr(), None, st.data_ptr() + 48 * i, stream.cuda_stream)
+            ctx.vcm_compute(r, vs[i].data_ptr(), cs[i].data_ptr(), None, st.data_ptr() + STATS_BYTES * i, stream.cuda_stream)
 
     res = {}
     for name, fn in (("persistent_batch", batch), ("one_per_launch", singles)):
@@ -398,13 +407,20 @@ def run_batched(args):
 
 def run_serve(args):
     """Poisson arrivals of requests from the batched mix against a resident
-    100,000-box scene: continuous batching (vcm_submit/vcm_poll) against a
-    FIFO server that runs one request per launch."""
+    100,000-box scene.  Continuous batching (vcm_submit / vcm_poll: queued
+    requests are admitted into slots as memory and slots free up, and run as
+    batched persistent launches that overlap on the device) against a FIFO
+    server that runs one request per launch: a worker thread takes requests
+    in arrival order, runs vcm_compute on one stream and copies v and colors
+    back to pinned host memory.  Latency = completion minus arrival."""
+    import queue as _queue
+
     import torch
 
     import synth
     from paper_1310_7297_gb300 import Context, n_viewpoints
     from paper_1310_7297_gb300 import build as B
+    from paper_1310_7297_gb300.vcm import STATS_BYTES
 
     B.build()
     dev = torch.device("cuda", 0)
@@ -412,38 +428,62 @@ def run_serve(args):
     ctx = Context(0, 64 << 30)
     ctx.load_scene(scene)
     ctx.vcm_build(50.0)
+    ctx.vcm_set_slots(args.slots, args.max_batch)
     pool = synth.serving_requests(scene, count=args.serve_pool)
     seg_of = [n_viewpoints(r) * r["patches_u"] * r["patches_w"] for r in pool]
-    stream = torch.cuda.current_stream(dev)
-    vs, cs, st = _alloc_outputs(torch, dev, pool)
-    # service time of each request alone, one launch each
-    for i, r in enumerate(pool[:4]):
-        ctx.vcm_compute(r, vs[i].data_ptr(), cs[i].data_ptr(), None, st.data_ptr() + 48 * i, stream.cuda_stream)
-    torch.cuda.synchronize()
-    service = []
-    for i, r in enumerate(pool):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ctx.vcm_compute(r, vs[i].data_ptr(), cs[i].data_ptr(), None, st.data_ptr() + 48 * i, stream.cuda_stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        service.append(a.elapsed_time(b))
-    del vs, cs, st
+    nmax = max(n_viewpoints(r) for r in pool)
+    stream = torch.cuda.Stream(dev)
+    d_v = torch.empty(nmax, dtype=torch.float32, device=dev)
+    d_c = torch.empty(nmax, dtype=torch.uint8, device=dev)
+    d_s = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
+    h_v = torch.empty(nmax, dtype=torch.float32).pin_memory()
+    h_c = torch.empty(nmax, dtype=torch.uint8).pin_memory()
+
+    def fifo_one(r):
+        n = n_viewpoints(r)
+        with torch.cuda.stream(stream):
+            ctx.vcm_compute(r, d_v.data_ptr(), d_c.data_ptr(), None, d_s.data_ptr(), stream.cuda_stream)
+            h_v[:n].copy_(d_v[:n], non_blocking=True)
+            h_c[:n].copy_(d_c[:n], non_blocking=True)
+        stream.synchronize()
+
+    for r in pool[:8]:
+        fifo_one(r)
+    # warm the scheduler path too
+    for t in [ctx.vcm_submit(r) for r in pool[:8]]:
+        ctx.vcm_poll(t, -1)
+        ctx.vcm_result_release(t)
     out = []
     for rate in args.rates:
         n = int(min(args.serve_count, max(40, rate * args.serve_seconds)))
         arr = synth.poisson_arrivals(int(rate), float(rate), n)
         picks = [pool[i % len(pool)] for i in range(n)]
         seg = sum(seg_of[i % len(pool)] for i in range(n))
-        # FIFO, one request per launch: start = max(arrival, previous done)
-        done, lat = 0.0, []
+
+        # FIFO server, one request per launch
+        q = _queue.Queue()
+        done = [0.0] * n
+
+        def worker():
+            for _ in range(n):
+                i, t0 = q.get()
+                fifo_one(picks[i])
+                done[i] = time.perf_counter() - t0
+
+        th = threading.Thread(target=worker)
+        th.start()
+        t0 = time.perf_counter()
         for i in range(n):
-            start = max(arr[i], done)
-            done = start + service[i % len(pool)] / 1e3
-            lat.append(1e3 * (done - arr[i]))
+            now = time.perf_counter() - t0
+            if arr[i] > now:
+                time.sleep(arr[i] - now)
+            q.put((i, t0))
+        th.join()
+        lat = [1e3 * (done[i] - arr[i]) for i in range(n)]
         fifo = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "segments_per_s": seg / done}
-        # continuous batching through the scheduler, in real time
+                "segments_per_s": seg / max(done)}
+
+        # continuous batching through the scheduler
         tickets = [None] * n
         t0 = time.perf_counter()
         for i in range(n):
@@ -451,12 +491,10 @@ def run_serve(args):
             if arr[i] > now:
                 time.sleep(arr[i] - now)
             tickets[i] = (ctx.vcm_submit(picks[i]), time.perf_counter() - t0)
-        lat2 = []
-        last = 0.0
+        lat2, last = [], 0.0
         for i, (t, ts) in enumerate(tickets):
             ctx.vcm_poll(t, -1)
-            _, _, _, stt = ctx.vcm_result_get(t, copy=False)
-            # queueing from the arrival instant plus the library's submit-to-done time
+            _, hc, _, stt = ctx.vcm_result_get(t, copy=False)
             lat2.append((ts - arr[i]) * 1e3 + stt["latency_ms"])
             last = max(last, arr[i] + lat2[-1] / 1e3)
             ctx.vcm_result_release(t)
@@ -464,7 +502,7 @@ def run_serve(args):
                 "segments_per_s": seg / last}
         out.append({"rate_per_s": rate, "requests": n, "continuous": cont, "one_per_launch_fifo": fifo})
     print(json.dumps({"mode": "serve", "metric": METRIC, "unit": UNIT, "boxes": scene.n, "budget_gb": 64,
-                      "mean_service_ms": float(np.mean(service)), "rates": out}), flush=True)
+                      "slots": args.slots, "max_batch": args.max_batch, "rates": out}), flush=True)
     ctx.close()
 
 
@@ -483,6 +521,8 @@ def main():
     ap.add_argument("--serve-count", type=int, default=400)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--rates", type=float, nargs="+", default=[50, 100, 200, 500, 1000, 2000])
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--max-batch", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

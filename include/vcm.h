@@ -112,10 +112,12 @@ typedef struct {
     uint32_t vmax_bits;                /* largest v (float bits), accumulated on device */
     uint32_t edge_cells;               /* viewpoints within 1e-5 (relative) of a color bin edge */
     uint32_t error;                    /* nonzero: a device-side check failed (see vcm_last_error) */
-    unsigned long long slab_tests;     /* lane-level slab tests executed */
-    unsigned long long rechecked;      /* segments re-decided by the exact float64 predicate */
+    unsigned long long slab_tests;     /* lane-level slab tests executed in the row sweep */
+    unsigned long long rechecked;      /* segment-box pairs re-decided by the exact float64 predicate */
     unsigned long long segments;       /* viewpoint-patch pairs decided (= viewpoints x patches) */
     unsigned long long boxes_listed;   /* sum over tiles of culled candidate-list lengths */
+    unsigned long long corner_tests;   /* segment-box tests of the one-box-blocks-all check */
+    unsigned long long shortcut_viewpoints;  /* viewpoints decided by that check */
 } vcm_stats;
 
 /* Results of a submitted request; all pointers owned by the context. */
@@ -135,7 +137,7 @@ typedef struct {
 /* Autotuned launch shape for one class of request (see vcm_autotune). */
 typedef struct {
     uint32_t tile_x, tile_y;   /* viewpoints per tile (a tile is one block's work item) */
-    uint32_t patch_k;          /* patches per lane held in registers per pass (1..16) */
+    uint32_t patch_k;          /* patch rows per lane held in registers per pass (0 = auto; at most 8) */
     uint32_t box_cap;          /* candidate boxes staged in shared memory per tile */
 } vcm_tune;
 

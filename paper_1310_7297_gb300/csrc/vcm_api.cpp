@@ -264,9 +264,9 @@ void fill_shape(const Canon &c, const vcm_tune &t, DevRequest &d)
     d.groups = 32 / d.nuc;
     d.col_passes = (c.nu + d.nuc - 1) / d.nuc;
     const int rows_per_lane = (c.nw + d.groups - 1) / d.groups;
-    int k = pow2_at_least(std::min(rows_per_lane, 16));
+    int k = pow2_at_least(std::min(rows_per_lane, 8));
     if (t.patch_k > 0)
-        k = std::min(k, pow2_at_least(std::min<int>(t.patch_k, 16)));
+        k = std::min(k, pow2_at_least(std::min<int>(t.patch_k, 8)));
     d.k_rows = k;
     d.row_passes = (c.nw + d.groups * k - 1) / (d.groups * k);
     d.tile_x = (int)std::max(1u, t.tile_x);
@@ -446,9 +446,9 @@ namespace {
 vcm_tune default_tune()
 {
     vcm_tune t;
-    t.tile_x = 8;
+    t.tile_x = 16;
     t.tile_y = 8;
-    t.patch_k = 0;
+    t.patch_k = 8;
     t.box_cap = 1024;
     return t;
 }
@@ -1495,7 +1495,7 @@ vcm_status vcm_set_tune(vcm_ctx *ctx, const vcm_tune *tune)
     }
     if (tune->tile_x > 256 || tune->tile_y < 1 || tune->tile_y > 256 || tune->patch_k > 16 ||
         tune->box_cap < 32 || tune->box_cap > 5000)
-        return fail(VCM_E_ARG, "tile sides 1..256, patch_k 0..16, box_cap 32..5000");
+        return fail(VCM_E_ARG, "tile sides 1..256, patch_k 0..16 (rows per pass are capped at 8), box_cap 32..5000");
     ctx->forced = true;
     ctx->forced_tune = *tune;
     return VCM_OK;
@@ -1698,9 +1698,9 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
         CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
         CUDA_TRY(cudaEventCreate(&e0));
         CUDA_TRY(cudaEventCreate(&e1));
-        const uint32_t tiles[][2] = {{4, 4}, {8, 4}, {8, 8}, {16, 8}, {16, 16}};
+        const uint32_t tiles[][2] = {{8, 4}, {8, 8}, {16, 8}, {32, 8}, {16, 16}};
         const uint32_t caps[] = {512, 1024, 2048};
-        const uint32_t ks[] = {0, 4, 8};
+        const uint32_t ks[] = {2, 4, 8};
         double best_ms[kTuneClasses];
         vcm_tune best[kTuneClasses];
         bool seen[kTuneClasses] = {false};

@@ -10,7 +10,7 @@
 
 namespace vcm {
 
-constexpr int kWarps = 8;                 // warps per block of the tile kernel
+constexpr int kWarps = 4;                 // warps per block of the tile kernel
 constexpr int kThreads = kWarps * 32;
 constexpr int kMaxPlanes = 32;            // separating planes kept per tile hull
 constexpr float kBand = 1e-6f;            // FP32 slab margin re-decided in FP64

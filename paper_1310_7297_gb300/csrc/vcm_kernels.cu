@@ -250,22 +250,24 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 // Candidate planes of the hull of points P[0..np): for every point triple
 // (3D) or pair (2D) whose plane leaves all points on one side, the outward
-// normal; duplicates from coplanar points keep only their first triple.
-__device__ void hull_planes(int dims, const double (*P)[3], int np, TileSmem &sm)
+// normal; of coplanar points only the first triple is kept.  Any normal gives
+// a valid half-space once its offset covers every point (below), so float32
+// is enough to find them.
+__device__ void hull_planes(int dims, const float (*P)[3], int np, TileSmem &sm)
 {
     const int t = threadIdx.x;
-    double scale = 0.0;
+    float scale = 0.f;
     for (int a = 1; a < np; ++a)
         for (int k = 0; k < 3; ++k)
-            scale = fmax(scale, fabs(P[a][k] - P[0][k]));
-    scale = fmax(scale, 1.0);
+            scale = fmaxf(scale, fabsf(P[a][k] - P[0][k]));
+    scale = fmaxf(scale, 1.f);
     const int n_cand = (dims == 3) ? 56 : 15;
     if (t < n_cand) {
         int i, j, k = -1;
-        double n[3];
+        float n[3];
         if (dims == 3) {
             i = c_tri[t][0]; j = c_tri[t][1]; k = c_tri[t][2];
-            double e1[3], e2[3];
+            float e1[3], e2[3];
             for (int c = 0; c < 3; ++c) {
                 e1[c] = P[j][c] - P[i][c];
                 e2[c] = P[k][c] - P[i][c];
@@ -284,21 +286,21 @@ __device__ void hull_planes(int dims, const double (*P)[3], int np, TileSmem &sm
             j = i + 1 + idx;
             n[0] = -(P[j][1] - P[i][1]);
             n[1] = P[j][0] - P[i][0];
-            n[2] = 0.0;
+            n[2] = 0.f;
         }
-        const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        const float len = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
         const int last = (dims == 3) ? k : j;
-        if (len > 1e-9 * scale * scale) {
-            const double tol = 1e-9 * len * scale;
+        if (len > 1e-6f * scale * scale) {
+            const float tol = 1e-5f * len * scale;
             bool pos = false, neg = false, dup = false;
             for (int l = 0; l < np; ++l) {
-                double s = n[0] * (P[l][0] - P[i][0]) + n[1] * (P[l][1] - P[i][1]) +
-                           n[2] * (P[l][2] - P[i][2]);
+                const float s = n[0] * (P[l][0] - P[i][0]) + n[1] * (P[l][1] - P[i][1]) +
+                                n[2] * (P[l][2] - P[i][2]);
                 if (s > tol)
                     pos = true;
                 if (s < -tol)
                     neg = true;
-                if (fabs(s) <= tol && l < last && l != i && l != j && l != k)
+                if (fabsf(s) <= tol && l < last && l != i && l != j && l != k)
                     dup = true;
             }
             if (!(pos && neg) && !dup) {
@@ -306,14 +308,13 @@ __device__ void hull_planes(int dims, const double (*P)[3], int np, TileSmem &sm
                     // side 0: n outward (all points at s <= 0); side 1: -n outward
                     if ((side == 0 && pos) || (side == 1 && neg))
                         continue;
-                    float nx = (float)((side ? -n[0] : n[0]) / len);
-                    float ny = (float)((side ? -n[1] : n[1]) / len);
-                    float nz = (float)((side ? -n[2] : n[2]) / len);
+                    const float sg = side ? -1.f : 1.f;
+                    const float nx = sg * n[0] / len, ny = sg * n[1] / len, nz = sg * n[2] / len;
                     float c = -f_inf();
                     for (int l = 0; l < np; ++l)
-                        c = fmaxf(c, dot3(nx, ny, nz, (float)P[l][0], (float)P[l][1], (float)P[l][2]));
+                        c = fmaxf(c, dot3(nx, ny, nz, P[l][0], P[l][1], P[l][2]));
                     c += 0.04f * (fabsf(nx) + fabsf(ny) + fabsf(nz));
-                    int slot = atomicAdd(&sm.n_planes, 1);
+                    const int slot = atomicAdd(&sm.n_planes, 1);
                     if (slot < kMaxPlanes)
                         sm.planes[slot] = Plane{nx, ny, nz, c};
                 }
@@ -322,18 +323,114 @@ __device__ void hull_planes(int dims, const double (*P)[3], int np, TileSmem &sm
     }
     // the six (four in 2D) axis planes of the hull's bounding box
     if (t >= 64 && t < 64 + 2 * dims) {
-        int ax = (t - 64) >> 1;
-        bool upper = ((t - 64) & 1) == 0;
-        double m = P[0][ax];
+        const int ax = (t - 64) >> 1;
+        const bool upper = ((t - 64) & 1) == 0;
+        float m = P[0][ax];
         for (int l = 1; l < np; ++l)
-            m = upper ? fmax(m, P[l][ax]) : fmin(m, P[l][ax]);
+            m = upper ? fmaxf(m, P[l][ax]) : fminf(m, P[l][ax]);
         float n3[3] = {0.f, 0.f, 0.f};
         n3[ax] = upper ? 1.f : -1.f;
-        float c = (upper ? (float)m : -(float)m) + 0.04f;
-        int slot = atomicAdd(&sm.n_planes, 1);
+        const float c = (upper ? m : -m) + 0.04f;
+        const int slot = atomicAdd(&sm.n_planes, 1);
         if (slot < kMaxPlanes)
             sm.planes[slot] = Plane{n3[0], n3[1], n3[2], c};
     }
+}
+
+// True if one of the first `nb` (<= 32) staged boxes certainly blocks the
+// segments from q to all four extreme patch centres.  On the target plane the
+// points whose segment to q meets a convex box form a convex set (a segment
+// from q to any point between two blocked ones crosses the box between their
+// two hit points), and every patch centre lies in the rectangle spanned by
+// the extreme ones, so such a box blocks every patch.  Lanes take one box
+// each; only float32 margins above the band count, so the answer is exact.
+__device__ __forceinline__ bool one_box_blocks_all(const DevRequest &R, const float4 *__restrict__ sbox, int nb,
+                                                   float qu, float qn, float qw)
+{
+    const int lane = threadIdx.x & 31;
+    const float du0 = R.u_min - qu, du1 = R.u_max - qu;
+    const float dn = R.p_n - qn;
+    const float dw0 = R.w_min - qw, dw1 = R.w_max - qw;
+    bool full = false;
+    if (lane < nb) {
+        const float iu0 = __frcp_rn(du0), iu1 = __frcp_rn(du1), inn = __frcp_rn(dn);
+        const float iw0 = __frcp_rn(dw0), iw1 = __frcp_rn(dw1);
+        const float4 lo = sbox[2 * lane], hi = sbox[2 * lane + 1];
+        const float au = lo.x - qu, bu = hi.x - qu, an = lo.y - qn, bn = hi.y - qn;
+        const float aw = lo.z - qw, bw = hi.z - qw;
+        const float nu0 = (du0 >= 0.f ? au : bu) * iu0, fu0 = (du0 >= 0.f ? bu : au) * iu0;
+        const float nu1 = (du1 >= 0.f ? au : bu) * iu1, fu1 = (du1 >= 0.f ? bu : au) * iu1;
+        const float nw0 = (dw0 >= 0.f ? aw : bw) * iw0, fw0 = (dw0 >= 0.f ? bw : aw) * iw0;
+        const float nw1 = (dw1 >= 0.f ? aw : bw) * iw1, fw1 = (dw1 >= 0.f ? bw : aw) * iw1;
+        const float e0 = fmaxf((dn >= 0.f ? an : bn) * inn, 0.f);
+        const float x0 = fminf((dn >= 0.f ? bn : an) * inn, 1.f);
+        const bool c00 = fminf(fminf(fu0, fw0), x0) - fmaxf(fmaxf(nu0, nw0), e0) > kBand;
+        const bool c10 = fminf(fminf(fu1, fw0), x0) - fmaxf(fmaxf(nu1, nw0), e0) > kBand;
+        const bool c01 = fminf(fminf(fu0, fw1), x0) - fmaxf(fmaxf(nu0, nw1), e0) > kBand;
+        const bool c11 = fminf(fminf(fu1, fw1), x0) - fmaxf(fmaxf(nu1, nw1), e0) > kBand;
+        full = c00 && c10 && c01 && c11;
+    }
+    return __any_sync(kFull, full);
+}
+
+// Planes of the pyramid with apex q and base the rectangle of extreme patch
+// centres (2D: the triangle q, segment ends), in the target frame (u, n, w).
+// Every segment from q to a patch centre lies in it, so a box outside one of
+// the planes meets none of them.  Each plane's offset is the largest float32
+// evaluation over all the pyramid's points plus the same margin as the tile
+// hull, so the half-space holds the whole pyramid whatever the plane's
+// orientation; a degenerate plane only culls less.  Lanes 0..5 each write
+// one plane (NaN-free: degenerate normals are dropped); returns the count.
+__device__ __forceinline__ int pyramid_planes(const DevRequest &R, float qu, float qn, float qw, Plane *out)
+{
+    const int lane = threadIdx.x & 31;
+    const float P[5][3] = {{qu, qn, qw},
+                           {R.u_min, R.p_n, R.w_min},
+                           {R.u_max, R.p_n, R.w_min},
+                           {R.u_max, R.p_n, R.w_max},
+                           {R.u_min, R.p_n, R.w_max}};
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    bool ok = false;
+    if (lane == 0) {
+        // the target plane: segments stay on q's side of it
+        ny = (R.p_n > qn) ? 1.f : -1.f;
+        ok = R.p_n != qn;
+    } else if (lane <= 4) {
+        const int e = lane - 1, f = lane & 3;   // rectangle edge e -> f
+        if (R.dims == 3) {
+            const float ax = P[1 + e][0] - qu, ay = P[1 + e][1] - qn, az = P[1 + e][2] - qw;
+            const float bx = P[1 + f][0] - qu, by = P[1 + f][1] - qn, bz = P[1 + f][2] - qw;
+            nx = ay * bz - az * by;
+            ny = az * bx - ax * bz;
+            nz = ax * by - ay * bx;
+        } else if (e < 2) {
+            // 2D: lines from q through the two segment ends, normal in the (u, n) plane
+            nx = -(P[1 + e][1] - qn);
+            ny = P[1 + e][0] - qu;
+        }
+        const float len = sqrtf(nx * nx + ny * ny + nz * nz);
+        ok = len > 0.f;
+        if (ok) {
+            nx /= len; ny /= len; nz /= len;
+            // outward: away from a point inside the pyramid
+            const float cu = 0.5f * (qu + 0.5f * (R.u_min + R.u_max)), cn = 0.5f * (qn + R.p_n);
+            const float cw = 0.5f * (qw + 0.5f * (R.w_min + R.w_max));
+            if (dot3(nx, ny, nz, cu, cn, cw) > dot3(nx, ny, nz, qu, qn, qw)) {
+                nx = -nx; ny = -ny; nz = -nz;
+            }
+        }
+    }
+    float c = -f_inf();
+    if (ok) {
+        for (int l = 0; l < 5; ++l)
+            c = fmaxf(c, dot3(nx, ny, nz, P[l][0], P[l][1], P[l][2]));
+        c += 0.04f * (fabsf(nx) + fabsf(ny) + fabsf(nz));
+    }
+    const unsigned okm = __ballot_sync(kFull, ok && lane <= 4);
+    if (ok && lane <= 4)
+        out[__popc(okm & ((1u << lane) - 1u))] = Plane{nx, ny, nz, c};
+    __syncwarp();
+    return __popc(okm);
 }
 
 // One viewpoint swept by one warp.  Lane l owns patch column
@@ -346,8 +443,8 @@ template <int K, bool MIXED>
 __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const float4 *__restrict__ sbox,
                                                  int n_smem, const int *__restrict__ spill, int count,
                                                  const float4 *__restrict__ gbox, float qu, float qn,
-                                                 float qw, bool front, long long vp,
-                                                 unsigned long long &tests, unsigned &rechecks)
+                                                 float qw, bool front, long long vp, const Plane *pyr,
+                                                 int npyr, unsigned long long &tests, unsigned &rechecks)
 {
     const int lane = threadIdx.x & 31;
     const int nuc = R.nuc, G = R.groups;
@@ -358,6 +455,7 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
     const bool sgn_n = dn >= 0.f;
     const bool sgn_w_uni = qw <= R.w_min;    // all rows at dw >= 0 (used when !MIXED)
     const bool want_bits = (R.flags & VCM_EMIT_BITS) && R.bits_out;
+    const float *__restrict__ w_coord = R.w_coord;
     float sum = 0.f, comp = 0.f;
 
     for (int cp = 0; cp < R.col_passes; ++cp) {
@@ -368,14 +466,13 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
         const float inv_u = __frcp_rn(du);
         const bool sgn_u = du >= 0.f;
         for (int rp = 0; rp < R.row_passes; ++rp) {
-            float inv_w[K], clampv[K], pw[K];
+            float inv_w[K], clampv[K];
             unsigned valid = 0, sgnw = 0;
 #pragma unroll
             for (int m = 0; m < K; ++m) {
                 const int iw = (rp * K + m) * G + g;
                 const bool ok = col_ok && iw < R.nw;
-                pw[m] = R.w_coord[ok ? iw : 0];
-                const float dw = pw[m] - qw;
+                const float dw = w_coord[ok ? iw : 0] - qw;
                 inv_w[m] = __frcp_rn(dw);
                 if (dw >= 0.f)
                     sgnw |= 1u << m;
@@ -387,7 +484,31 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
             if (!__any_sync(kFull, alive != 0))
                 continue;
             int nb = 0;
-            for (int i = 0; i < count; ++i) {
+            bool done = false;
+            for (int base = 0; base < count && !done; base += 32) {
+              // lanes over boxes: which of the next 32 candidates meet the
+              // viewpoint's pyramid at all
+              unsigned todo;
+              {
+                const int i = base + lane;
+                bool cand = false;
+                if (i < count) {
+                    float4 lo, hi;
+                    if (i < n_smem) {
+                        lo = sbox[2 * i];
+                        hi = sbox[2 * i + 1];
+                    } else {
+                        const int s = spill[i - n_smem];
+                        lo = __ldg(&gbox[2 * s]);
+                        hi = __ldg(&gbox[2 * s + 1]);
+                    }
+                    cand = !outside(pyr, npyr, lo, hi);
+                }
+                todo = __ballot_sync(kFull, cand);
+              }
+              while (todo) {
+                const int i = base + __ffs(todo) - 1;
+                todo &= todo - 1;
                 float4 lo, hi;
                 if (i < n_smem) {
                     lo = sbox[2 * i];
@@ -399,7 +520,6 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                 }
                 const float a_u = lo.x - qu, b_u = hi.x - qu;
                 const float a_n = lo.y - qn, b_n = hi.y - qn;
-                const float a_w = lo.z - qw, b_w = hi.z - qw;
                 const float tnu = (sgn_u ? a_u : b_u) * inv_u;
                 const float tfu = (sgn_u ? b_u : a_u) * inv_u;
                 const float tnn = (sgn_n ? a_n : b_n) * inv_n;
@@ -410,6 +530,7 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                 if (__all_sync(kFull, alive == 0 || (pre_x - pre_e) < -kBand))
                     continue;
                 ++nb;   // boxes whose rows are tested
+                const float a_w = lo.z - qw, b_w = hi.z - qw;
                 const float near_w = sgn_w_uni ? a_w : b_w;
                 const float far_w = sgn_w_uni ? b_w : a_w;
 #pragma unroll
@@ -429,7 +550,8 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                     if (mv >= -kBand) {
                         bool hit = mv > kBand;
                         if (!hit) {
-                            hit = exact_hit(qu, qn, qw, pu, R.p_n, pw[m], lo, hi);
+                            const int iw = (rp * K + m) * G + g;
+                            hit = exact_hit(qu, qn, qw, pu, R.p_n, w_coord[iw], lo, hi);
                             ++rechecks;
                         }
                         if (hit) {
@@ -438,40 +560,45 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                         }
                     }
                 }
-                if (__all_sync(kFull, alive == 0))
+                if (__all_sync(kFull, alive == 0)) {
+                    done = true;
                     break;
+                }
+              }
             }
             tests += (unsigned long long)nb * K;
             // visible measure of the unblocked rows, and the blocked bits
+            if (want_bits || __any_sync(kFull, alive != 0)) {
 #pragma unroll
-            for (int m = 0; m < K; ++m) {
-                if (!((valid >> m) & 1u))
-                    continue;
-                const bool blocked = !((alive >> m) & 1u);
-                const int iw = (rp * K + m) * G + g;
-                if (blocked) {
-                    if (want_bits) {
-                        const int j = iw * R.nu + iu;
-                        atomicOr(&R.bits_out[vp * R.words + (j >> 5)], 1u << (j & 31));
+                for (int m = 0; m < K; ++m) {
+                    if (!((valid >> m) & 1u))
+                        continue;
+                    const bool blocked = !((alive >> m) & 1u);
+                    const int iw = (rp * K + m) * G + g;
+                    if (blocked) {
+                        if (want_bits) {
+                            const int j = iw * R.nu + iu;
+                            atomicOr(&R.bits_out[vp * R.words + (j >> 5)], 1u << (j & 31));
+                        }
+                    } else if (front) {
+                        const float ru = qu - pu, rn = qn - R.p_n, rw = qw - w_coord[iw];
+                        const float d2 = fmaf(ru, ru, fmaf(rn, rn, rw * rw));
+                        const float s = R.sn * rn;   // |r| cos(theta)
+                        float term;
+                        if (R.dims == 3) {
+                            const float ir = rsqrtf(d2);
+                            term = R.measure * s * (ir * ir * ir);
+                        } else {
+                            term = R.measure * s / d2;
+                        }
+                        // Neumaier compensated accumulation
+                        const float tsum = sum + term;
+                        if (fabsf(sum) >= fabsf(term))
+                            comp += (sum - tsum) + term;
+                        else
+                            comp += (term - tsum) + sum;
+                        sum = tsum;
                     }
-                } else if (front) {
-                    const float ru = qu - pu, rn = qn - R.p_n, rw = qw - pw[m];
-                    const float d2 = fmaf(ru, ru, fmaf(rn, rn, rw * rw));
-                    const float s = R.sn * rn;   // |r| cos(theta)
-                    float term;
-                    if (R.dims == 3) {
-                        const float ir = rsqrtf(d2);
-                        term = R.measure * s * (ir * ir * ir);
-                    } else {
-                        term = R.measure * s / d2;
-                    }
-                    // Neumaier compensated accumulation
-                    const float tsum = sum + term;
-                    if (fabsf(sum) >= fabsf(term))
-                        comp += (sum - tsum) + term;
-                    else
-                        comp += (term - tsum) + sum;
-                    sum = tsum;
                 }
             }
         }
@@ -487,18 +614,18 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
 template <int K>
 __device__ __forceinline__ float sweep_k(const DevRequest &R, const float4 *sbox, int n_smem,
                                          const int *spill, int count, const float4 *gbox, float qu,
-                                         float qn, float qw, bool front, long long vp,
-                                         unsigned long long &tests, unsigned &rechecks)
+                                         float qn, float qw, bool front, long long vp, const Plane *pyr,
+                                         int npyr, unsigned long long &tests, unsigned &rechecks)
 {
     const bool mixed = !(qw <= R.w_min) && !(qw > R.w_max);
     if (mixed)
-        return sweep_viewpoint<K, true>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp,
-                                        tests, rechecks);
-    return sweep_viewpoint<K, false>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp,
+        return sweep_viewpoint<K, true>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr,
+                                        npyr, tests, rechecks);
+    return sweep_viewpoint<K, false>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr,
                                      tests, rechecks);
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 4)
 k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict__ tile_prefix,
         int n_req, int total_tiles, int *__restrict__ work, int *__restrict__ spill_all, int box_cap)
 {
@@ -506,8 +633,10 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
     float4 *s_box = reinterpret_cast<float4 *>(smem_raw);
     int *s_ids = reinterpret_cast<int *>(smem_raw + (size_t)box_cap * 32);
     __shared__ TileSmem sm;
-    __shared__ double s_pts[8][3];
+    __shared__ float s_pts[8][3];
     __shared__ DevRequest s_req;
+    __shared__ int s_next;
+    __shared__ Plane s_pyr[kWarps][6];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int *spill = spill_all + (size_t)blockIdx.x * sc.n_boxes;
@@ -566,26 +695,27 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         if (tid == 0) {
             sm.n_planes = 0;
             sm.count = 0;
-            const double X[2] = {R.x_coord[ix0], R.x_coord[ix1 - 1]};
-            const double Y[2] = {R.y_coord[iy0], R.y_coord[iy1 - 1]};
+            s_next = 0;
+            const float X[2] = {R.x_coord[ix0], R.x_coord[ix1 - 1]};
+            const float Y[2] = {R.y_coord[iy0], R.y_coord[iy1 - 1]};
             for (int c = 0; c < 4; ++c) {
                 s_pts[c][0] = X[c & 1];
                 s_pts[c][1] = Y[c >> 1];
-                s_pts[c][2] = (R.dims == 3) ? (double)zq : 0.0;
+                s_pts[c][2] = (R.dims == 3) ? zq : 0.f;
             }
             if (R.dims == 3) {
-                const double U[2] = {R.u_min, R.u_max}, W[2] = {R.w_min, R.w_max};
+                const float U[2] = {R.u_min, R.u_max}, W[2] = {R.w_min, R.w_max};
                 for (int c = 0; c < 4; ++c) {
                     s_pts[4 + c][R.au] = U[c & 1];
                     s_pts[4 + c][R.aw] = W[c >> 1];
                     s_pts[4 + c][R.an] = R.p_n;
                 }
             } else {
-                const double U[2] = {R.u_min, R.u_max};
+                const float U[2] = {R.u_min, R.u_max};
                 for (int c = 0; c < 2; ++c) {
                     s_pts[4 + c][R.au] = U[c];
                     s_pts[4 + c][R.an] = R.p_n;
-                    s_pts[4 + c][2] = 0.0;
+                    s_pts[4 + c][2] = 0.f;
                 }
             }
         }
@@ -597,16 +727,16 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
 
         // walk the grid cells under the hull's footprint
         {
-            double bx0 = s_pts[0][0], bx1 = s_pts[0][0], by0 = s_pts[0][1], by1 = s_pts[0][1];
+            float bx0 = s_pts[0][0], bx1 = s_pts[0][0], by0 = s_pts[0][1], by1 = s_pts[0][1];
             for (int l = 1; l < np; ++l) {
-                bx0 = fmin(bx0, s_pts[l][0]); bx1 = fmax(bx1, s_pts[l][0]);
-                by0 = fmin(by0, s_pts[l][1]); by1 = fmax(by1, s_pts[l][1]);
+                bx0 = fminf(bx0, s_pts[l][0]); bx1 = fmaxf(bx1, s_pts[l][0]);
+                by0 = fminf(by0, s_pts[l][1]); by1 = fmaxf(by1, s_pts[l][1]);
             }
             const float oh = sc.overhang;
-            int cx0 = (int)floorf(((float)bx0 - oh - sc.gx0) * sc.inv_cell) - 1;
-            int cx1 = (int)floorf(((float)bx1 + oh - sc.gx0) * sc.inv_cell) + 1;
-            int cy0 = (int)floorf(((float)by0 - oh - sc.gy0) * sc.inv_cell) - 1;
-            int cy1 = (int)floorf(((float)by1 + oh - sc.gy0) * sc.inv_cell) + 1;
+            int cx0 = (int)floorf((bx0 - oh - sc.gx0) * sc.inv_cell) - 1;
+            int cx1 = (int)floorf((bx1 + oh - sc.gx0) * sc.inv_cell) + 1;
+            int cy0 = (int)floorf((by0 - oh - sc.gy0) * sc.inv_cell) - 1;
+            int cy1 = (int)floorf((by1 + oh - sc.gy0) * sc.inv_cell) + 1;
             cx0 = max(cx0, 0); cy0 = max(cy0, 0);
             cx1 = min(cx1, sc.gnx - 1); cy1 = min(cy1, sc.gny - 1);
             const int wcx = cx1 - cx0 + 1;
@@ -633,44 +763,59 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         const int n_smem = min(count, box_cap);
         const float4 *gbox = sc.boxes[R.perm];
         // near-first order of the staged candidates: nearby boxes block the
-        // most sightlines, so the all-blocked exit comes early.  Keys are the
+        // most sightlines, so the all-blocked exits come early.  Keys are the
         // squared footprint distance from the tile centre (a positive float,
         // so its bits order like the value) above the sorted box index.
         if (n_smem > 1) {
-            unsigned long long *keyed = reinterpret_cast<unsigned long long *>(s_box);
-            int N = 1;
-            while (N < n_smem)
-                N <<= 1;
             const float cx = 0.5f * (R.x_coord[ix0] + R.x_coord[ix1 - 1]);
             const float cy = 0.5f * (R.y_coord[iy0] + R.y_coord[iy1 - 1]);
-            for (int i = tid; i < N; i += kThreads) {
-                unsigned long long k = ~0ull;
-                if (i < n_smem) {
-                    const int s = s_ids[i];
-                    const float4 l = world_box_lo(sc, s), h = world_box_hi(sc, s);
-                    const float dx = 0.5f * (l.x + h.x) - cx, dy = 0.5f * (l.y + h.y) - cy;
-                    k = ((unsigned long long)__float_as_uint(fmaf(dx, dx, dy * dy)) << 32) | (unsigned)s;
+            auto key_of = [&](int i) {
+                const int s = s_ids[i];
+                const float4 l = world_box_lo(sc, s), h = world_box_hi(sc, s);
+                const float dx = 0.5f * (l.x + h.x) - cx, dy = 0.5f * (l.y + h.y) - cy;
+                return ((unsigned long long)__float_as_uint(fmaf(dx, dx, dy * dy)) << 32) | (unsigned)s;
+            };
+            if (n_smem <= 32) {
+                // one warp, in registers
+                if (warp == 0) {
+                    unsigned long long key = lane < n_smem ? key_of(lane) : ~0ull;
+#pragma unroll
+                    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+                        for (int j = k >> 1; j > 0; j >>= 1) {
+                            const unsigned long long other = __shfl_xor_sync(kFull, key, j);
+                            const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
+                            key = keep_min ? (key < other ? key : other) : (key > other ? key : other);
+                        }
+                    if (lane < n_smem)
+                        s_ids[lane] = (int)(key & 0xffffffffu);
                 }
-                keyed[i] = k;
-            }
-            __syncthreads();
-            for (int k = 2; k <= N; k <<= 1) {
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    for (int i = tid; i < N; i += kThreads) {
-                        const int p = i ^ j;
-                        if (p > i) {
-                            const unsigned long long a = keyed[i], b = keyed[p];
-                            if ((a > b) == ((i & k) == 0)) {
-                                keyed[i] = b;
-                                keyed[p] = a;
+            } else {
+                unsigned long long *keyed = reinterpret_cast<unsigned long long *>(s_box);
+                int N = 1;
+                while (N < n_smem)
+                    N <<= 1;
+                for (int i = tid; i < N; i += kThreads)
+                    keyed[i] = i < n_smem ? key_of(i) : ~0ull;
+                __syncthreads();
+                for (int k = 2; k <= N; k <<= 1) {
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        for (int i = tid; i < N; i += kThreads) {
+                            const int p = i ^ j;
+                            if (p > i) {
+                                const unsigned long long a = keyed[i], b = keyed[p];
+                                if ((a > b) == ((i & k) == 0)) {
+                                    keyed[i] = b;
+                                    keyed[p] = a;
+                                }
                             }
                         }
+                        __syncthreads();
                     }
-                    __syncthreads();
                 }
+                for (int i = tid; i < n_smem; i += kThreads)
+                    s_ids[i] = (int)(keyed[i] & 0xffffffffu);
             }
-            for (int i = tid; i < n_smem; i += kThreads)
-                s_ids[i] = (int)(keyed[i] & 0xffffffffu);
             __syncthreads();
         }
         for (int i = tid; i < n_smem; i += kThreads) {
@@ -681,28 +826,50 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         cp_async_wait_all();
         __syncthreads();
 
-        // sweep: each warp takes viewpoints of the tile in turn
-        unsigned long long tests = 0;
-        unsigned rechecks = 0;
+        // sweep: warps take the tile's viewpoints one at a time
+        unsigned long long tests = 0, corner_tests = 0;
+        unsigned rechecks = 0, shortcuts = 0;
         float vmax = 0.f;
-        for (int vi = warp; vi < tn; vi += kWarps) {
+        for (;;) {
+            int vi = 0;
+            if (lane == 0)
+                vi = atomicAdd(&s_next, 1);
+            vi = __shfl_sync(kFull, vi, 0);
+            if (vi >= tn)
+                break;
             const int ix = ix0 + vi % tw, iy = iy0 + vi / tw;
             const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
-            const float qw3[3] = {R.x_coord[ix], R.y_coord[iy], zq};
-            const float qu = qw3[R.au], qn = qw3[R.an], qw = (R.dims == 3) ? qw3[R.aw] : 0.f;
+            const float qx = R.x_coord[ix], qy = R.y_coord[iy];
+            const float qu = R.au == 0 ? qx : (R.au == 1 ? qy : zq);
+            const float qn = R.an == 0 ? qx : (R.an == 1 ? qy : zq);
+            const float qw = R.dims == 3 ? (R.aw == 0 ? qx : (R.aw == 1 ? qy : zq)) : 0.f;
             const bool front = R.sn * (qn - R.p_n) > 0.f;
             if (!front && !want_bits) {
                 if (lane == 0)
                     R.v_out[vp] = 0.f;
                 continue;
             }
+            const int nb_short = min(n_smem, 32);
+            corner_tests += 4ull * nb_short;
+            if (n_smem > 0 && one_box_blocks_all(R, s_box, nb_short, qu, qn, qw)) {
+                ++shortcuts;
+                if (lane == 0)
+                    R.v_out[vp] = 0.f;
+                if (want_bits)
+                    for (int wd = lane; wd < R.words; wd += 32) {
+                        const int rem = R.P - 32 * wd;
+                        R.bits_out[vp * R.words + wd] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+                    }
+                continue;
+            }
+            Plane *pyr = s_pyr[warp];
+            const int npyr = pyramid_planes(R, qu, qn, qw, pyr);
             float v;
             switch (R.k_rows) {
-            case 1: v = sweep_k<1>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, tests, rechecks); break;
-            case 2: v = sweep_k<2>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, tests, rechecks); break;
-            case 4: v = sweep_k<4>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, tests, rechecks); break;
-            case 8: v = sweep_k<8>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, tests, rechecks); break;
-            default: v = sweep_k<16>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, tests, rechecks); break;
+            case 1: v = sweep_k<1>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+            case 2: v = sweep_k<2>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+            case 4: v = sweep_k<4>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+            default: v = sweep_k<8>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
             }
             if (!front)
                 v = 0.f;
@@ -713,7 +880,12 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // per-tile counters
         if (lane == 0) {
             atomicMax(&R.stats->vmax_bits, __float_as_uint(vmax));
-            atomicAdd(&R.stats->slab_tests, tests * 32ull);
+            if (tests)
+                atomicAdd(&R.stats->slab_tests, tests * 32ull);
+            if (corner_tests)
+                atomicAdd(&R.stats->corner_tests, corner_tests);
+            if (shortcuts)
+                atomicAdd(&R.stats->shortcut_viewpoints, (unsigned long long)shortcuts);
         }
         for (int off = 16; off > 0; off >>= 1)
             rechecks += __shfl_xor_sync(kFull, rechecks, off);

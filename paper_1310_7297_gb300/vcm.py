@@ -50,7 +50,8 @@ class vcm_stats(ctypes.Structure):
     _fields_ = [("v_ref", ctypes.c_float), ("vmax_bits", ctypes.c_uint32), ("edge_cells", ctypes.c_uint32),
                 ("error", ctypes.c_uint32), ("slab_tests", ctypes.c_ulonglong),
                 ("rechecked", ctypes.c_ulonglong), ("segments", ctypes.c_ulonglong),
-                ("boxes_listed", ctypes.c_ulonglong)]
+                ("boxes_listed", ctypes.c_ulonglong), ("corner_tests", ctypes.c_ulonglong),
+                ("shortcut_viewpoints", ctypes.c_ulonglong)]
 
 
 class vcm_result(ctypes.Structure):

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import synth
+from paper_1310_7297_gb300.vcm import STATS_BYTES
 from gpu_util import compare_bits, compare_colors, compare_v, full_parity, gpu_run
 from helpers import U, req2, req3, scene
 from oracle import oracle as O
@@ -239,7 +240,7 @@ def test_batch_equals_single_requests(ctx):
     vs = [torch.empty(n_viewpoints(r), device=dev) for r in reqs]
     cs = [torch.empty(n_viewpoints(r), dtype=torch.uint8, device=dev) for r in reqs]
     bs = [torch.empty(n_viewpoints(r) * words(r), dtype=torch.int32, device=dev) for r in reqs]
-    st = torch.empty(48 * len(reqs), dtype=torch.uint8, device=dev)
+    st = torch.empty(STATS_BYTES * len(reqs), dtype=torch.uint8, device=dev)
     ctx.vcm_compute_batch([dict(r, flags=1) for r in reqs], [t.data_ptr() for t in vs], [t.data_ptr() for t in cs],
                           [t.data_ptr() for t in bs], st.data_ptr(), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
@@ -311,3 +312,76 @@ def test_argument_errors(ctx):
     with pytest.raises(VcmError) as e:
         ctx.vcm_submit(req)
     assert e.value.status == -7
+
+
+# ---------------------------------------------------------------------------
+# full-size parity for the large and batched workloads (sampled viewpoints)
+# ---------------------------------------------------------------------------
+
+def _sampled_bits(ctx, req, idx):
+    """Run a request with bits on the device and bring back only the sampled rows."""
+    import torch
+
+    from paper_1310_7297_gb300 import n_viewpoints
+
+    v, c, b, s = ctx.compute(req, emit_bits=True)
+    n = n_viewpoints(req)
+    t = torch.as_tensor(idx, device=v.device)
+    bv = v.index_select(0, t).cpu().numpy().astype(np.float64)
+    bb = b.view(n, -1).index_select(0, t).cpu().numpy().view(np.uint32)
+    full_v = v.cpu().numpy().astype(np.float64)
+    del b
+    torch.cuda.synchronize()
+    return bv, bb, full_v
+
+
+def test_workload_3d_large_full_size_sampled(ctx):
+    """100,000 boxes over 10 km, 2048 x 2048 x 8 viewpoints, 64 x 32 patches,
+    50 m grid index: bits and v on 400 sampled viewpoints (half of them with
+    something visible)."""
+    sc, req = synth.workload_3d_large()
+    load(ctx, sc, 50.0)
+    n = 2048 * 2048 * 8
+    rng = np.random.default_rng(21)
+    idx0 = np.sort(rng.choice(n, 200, replace=False))
+    gv0, gb0, v_all = _sampled_bits(ctx, req, idx0)
+    nz = np.nonzero(v_all > 0)[0]
+    idx1 = np.sort(rng.choice(nz, min(200, nz.size), replace=False))
+    idx = np.unique(np.concatenate([idx0, idx1]))
+    gv, gb, _ = _sampled_bits(ctx, req, idx)
+    ov, ob = O.run(sc, req, indices=idx, bits=True)
+    compare_bits(ob, gb, "large scene sample")
+    compare_v(ov, gv, "large scene sample")
+    assert nz.size > 1000
+
+
+def test_workload_batched_full_mix_sampled(ctx):
+    """The 256-request mix over the shared 50,000-box scene in one persistent
+    launch; 8 requests checked against the oracle on sampled viewpoints."""
+    import torch
+
+    from paper_1310_7297_gb300 import n_viewpoints, words
+
+    sc, reqs = synth.workload_batched()
+    load(ctx, sc, 50.0)
+    dev = torch.device("cuda", 0)
+    vs = [torch.empty(n_viewpoints(r), device=dev) for r in reqs]
+    cs = [torch.empty(n_viewpoints(r), dtype=torch.uint8, device=dev) for r in reqs]
+    bs = [torch.empty(n_viewpoints(r) * words(r), dtype=torch.int32, device=dev) for r in reqs]
+    st = torch.empty(STATS_BYTES * len(reqs), dtype=torch.uint8, device=dev)
+    ctx.vcm_compute_batch([dict(r, flags=1) for r in reqs], [t.data_ptr() for t in vs], [t.data_ptr() for t in cs],
+                          [t.data_ptr() for t in bs], st.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    for k in rng.choice(len(reqs), 8, replace=False):
+        r = reqs[k]
+        n = n_viewpoints(r)
+        gv = vs[k].cpu().numpy().astype(np.float64)
+        nz = np.nonzero(gv > 0)[0]
+        idx = np.sort(rng.choice(n, min(n, 60), replace=False))
+        if nz.size:
+            idx = np.unique(np.concatenate([idx, rng.choice(nz, min(nz.size, 60), replace=False)]))
+        gb = bs[k].view(n, -1)[torch.as_tensor(idx, device=dev)].cpu().numpy().view(np.uint32)
+        ov, ob = O.run(sc, r, indices=idx, bits=True)
+        compare_bits(ob, gb, "batched request %d" % k)
+        compare_v(ov, gv[idx], "batched request %d" % k)

@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import synth
+from paper_1310_7297_gb300.vcm import STATS_BYTES
 from gpu_util import compare_bits, compare_colors, compare_v
 
 pytestmark = pytest.mark.gpu
@@ -29,7 +30,7 @@ def _outputs(req, bits):
     v = torch.empty(n, dtype=torch.float32, device=dev)
     c = torch.empty(n, dtype=torch.uint8, device=dev)
     b = torch.empty(n * words(req), dtype=torch.int32, device=dev) if bits else None
-    s = torch.empty(48, dtype=torch.uint8, device=dev)
+    s = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
     return v, c, b, s
 
 
