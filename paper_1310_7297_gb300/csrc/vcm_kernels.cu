@@ -25,6 +25,16 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 
+// Hardware reciprocal, at most 1 ulp from 1/d (2^-23 relative); 1/(+0) = +inf.
+// The slab-test error bound with it is about 5 u per t value, 10 u per
+// margin, still inside the 1e-6 band that is re-decided in float64.
+__device__ __forceinline__ float rcp_approx(float d)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // grid build
 // ---------------------------------------------------------------------------
@@ -353,8 +363,8 @@ __device__ __forceinline__ bool one_box_blocks_all(const DevRequest &R, const fl
     const float dw0 = R.w_min - qw, dw1 = R.w_max - qw;
     bool full = false;
     if (lane < nb) {
-        const float iu0 = __frcp_rn(du0), iu1 = __frcp_rn(du1), inn = __frcp_rn(dn);
-        const float iw0 = __frcp_rn(dw0), iw1 = __frcp_rn(dw1);
+        const float iu0 = rcp_approx(du0), iu1 = rcp_approx(du1), inn = rcp_approx(dn);
+        const float iw0 = rcp_approx(dw0), iw1 = rcp_approx(dw1);
         const float4 lo = sbox[2 * lane], hi = sbox[2 * lane + 1];
         const float au = lo.x - qu, bu = hi.x - qu, an = lo.y - qn, bn = hi.y - qn;
         const float aw = lo.z - qw, bw = hi.z - qw;
@@ -384,6 +394,7 @@ __device__ __forceinline__ bool one_box_blocks_all(const DevRequest &R, const fl
 __device__ __forceinline__ int pyramid_planes(const DevRequest &R, float qu, float qn, float qw, Plane *out)
 {
     const int lane = threadIdx.x & 31;
+    // rectangle corners in order (u_min,w_min) (u_max,w_min) (u_max,w_max) (u_min,w_max)
     const float P[5][3] = {{qu, qn, qw},
                            {R.u_min, R.p_n, R.w_min},
                            {R.u_max, R.p_n, R.w_min},
@@ -397,16 +408,18 @@ __device__ __forceinline__ int pyramid_planes(const DevRequest &R, float qu, flo
         ok = R.p_n != qn;
     } else if (lane <= 4) {
         const int e = lane - 1, f = lane & 3;   // rectangle edge e -> f
+        const float eu = (e == 0 || e == 3) ? R.u_min : R.u_max, ew = (e < 2) ? R.w_min : R.w_max;
+        const float fu = (f == 0 || f == 3) ? R.u_min : R.u_max, fw = (f < 2) ? R.w_min : R.w_max;
         if (R.dims == 3) {
-            const float ax = P[1 + e][0] - qu, ay = P[1 + e][1] - qn, az = P[1 + e][2] - qw;
-            const float bx = P[1 + f][0] - qu, by = P[1 + f][1] - qn, bz = P[1 + f][2] - qw;
+            const float ax = eu - qu, ay = R.p_n - qn, az = ew - qw;
+            const float bx = fu - qu, by = R.p_n - qn, bz = fw - qw;
             nx = ay * bz - az * by;
             ny = az * bx - ax * bz;
             nz = ax * by - ay * bx;
         } else if (e < 2) {
             // 2D: lines from q through the two segment ends, normal in the (u, n) plane
-            nx = -(P[1 + e][1] - qn);
-            ny = P[1 + e][0] - qu;
+            nx = -(R.p_n - qn);
+            ny = eu - qu;
         }
         const float len = sqrtf(nx * nx + ny * ny + nz * nz);
         ok = len > 0.f;
@@ -451,7 +464,7 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
     const int c_in = lane % nuc, g = lane / nuc;
     const bool lane_ok = g < G;
     const float dn = R.p_n - qn;
-    const float inv_n = __frcp_rn(dn);
+    const float inv_n = rcp_approx(dn);
     const bool sgn_n = dn >= 0.f;
     const bool sgn_w_uni = qw <= R.w_min;    // all rows at dw >= 0 (used when !MIXED)
     const bool want_bits = (R.flags & VCM_EMIT_BITS) && R.bits_out;
@@ -463,8 +476,11 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
         const bool col_ok = lane_ok && iu < R.nu;
         const float pu = R.u_coord[col_ok ? iu : 0];
         const float du = pu - qu;
-        const float inv_u = __frcp_rn(du);
+        const float inv_u = rcp_approx(du);
         const bool sgn_u = du >= 0.f;
+        const float ru = qu - pu, rn = qn - R.p_n;
+        const float col_d2 = fmaf(ru, ru, rn * rn);
+        const float m_s = R.measure * (R.sn * rn);   // measure x |r| cos(theta)
         for (int rp = 0; rp < R.row_passes; ++rp) {
             float inv_w[K], clampv[K];
             unsigned valid = 0, sgnw = 0;
@@ -473,7 +489,7 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                 const int iw = (rp * K + m) * G + g;
                 const bool ok = col_ok && iw < R.nw;
                 const float dw = w_coord[ok ? iw : 0] - qw;
-                inv_w[m] = __frcp_rn(dw);
+                inv_w[m] = rcp_approx(dw);
                 if (dw >= 0.f)
                     sgnw |= 1u << m;
                 clampv[m] = ok ? 0.f : f_inf();
@@ -492,7 +508,9 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
               {
                 const int i = base + lane;
                 bool cand = false;
-                if (i < count) {
+                if (i < count && npyr == 0) {
+                    cand = true;
+                } else if (i < count) {
                     float4 lo, hi;
                     if (i < n_smem) {
                         lo = sbox[2 * i];
@@ -581,15 +599,15 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                             atomicOr(&R.bits_out[vp * R.words + (j >> 5)], 1u << (j & 31));
                         }
                     } else if (front) {
-                        const float ru = qu - pu, rn = qn - R.p_n, rw = qw - w_coord[iw];
-                        const float d2 = fmaf(ru, ru, fmaf(rn, rn, rw * rw));
-                        const float s = R.sn * rn;   // |r| cos(theta)
+                        // |r|^2 = (ru^2 + rn^2) of the column + rw^2 of the row
+                        const float rw = qw - w_coord[iw];
+                        const float d2 = fmaf(rw, rw, col_d2);
                         float term;
                         if (R.dims == 3) {
                             const float ir = rsqrtf(d2);
-                            term = R.measure * s * (ir * ir * ir);
+                            term = m_s * (ir * ir * ir);   // A |r| cos(theta) / |r|^3
                         } else {
-                            term = R.measure * s / d2;
+                            term = m_s / d2;               // len |r| cos(theta) / |r|^2
                         }
                         // Neumaier compensated accumulation
                         const float tsum = sum + term;
@@ -642,26 +660,63 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
     int *spill = spill_all + (size_t)blockIdx.x * sc.n_boxes;
 
     for (;;) {
-        if (tid == 0)
-            sm.item = atomicAdd(work, 1);
+        // thread 0 takes the next tile, copies its request and lays out the
+        // hull points (one barrier for all of it)
+        if (tid == 0) {
+            const int it = atomicAdd(work, 1);
+            sm.item = it;
+            if (it < total_tiles) {
+                // request of this tile: last r with tile_prefix[r] <= it
+                int lo_r = 0, hi_r = n_req - 1;
+                while (lo_r < hi_r) {
+                    const int mid = (lo_r + hi_r + 1) >> 1;
+                    if (tile_prefix[mid] <= it)
+                        lo_r = mid;
+                    else
+                        hi_r = mid - 1;
+                }
+                s_req = reqs[lo_r];
+                sm.pad = it - tile_prefix[lo_r];   // tile index within its request
+                const DevRequest &Q = s_req;
+                const int t0 = sm.pad, pl = Q.tiles_x * Q.tiles_y;
+                const int ly = t0 / pl, t1 = t0 - ly * pl;
+                const int ty0 = t1 / Q.tiles_x, tx0 = t1 - ty0 * Q.tiles_x;
+                const int x0 = tx0 * Q.tile_x, x1 = min(Q.nx, x0 + Q.tile_x) - 1;
+                const int y0 = ty0 * Q.tile_y, y1 = min(Q.ny, y0 + Q.tile_y) - 1;
+                const float z = Q.z_coord[ly];
+                sm.n_planes = 0;
+                sm.count = 0;
+                s_next = 0;
+                const float X[2] = {Q.x_coord[x0], Q.x_coord[x1]};
+                const float Y[2] = {Q.y_coord[y0], Q.y_coord[y1]};
+                for (int c = 0; c < 4; ++c) {
+                    s_pts[c][0] = X[c & 1];
+                    s_pts[c][1] = Y[c >> 1];
+                    s_pts[c][2] = (Q.dims == 3) ? z : 0.f;
+                }
+                if (Q.dims == 3) {
+                    const float U[2] = {Q.u_min, Q.u_max}, W[2] = {Q.w_min, Q.w_max};
+                    for (int c = 0; c < 4; ++c) {
+                        s_pts[4 + c][Q.au] = U[c & 1];
+                        s_pts[4 + c][Q.aw] = W[c >> 1];
+                        s_pts[4 + c][Q.an] = Q.p_n;
+                    }
+                } else {
+                    const float U[2] = {Q.u_min, Q.u_max};
+                    for (int c = 0; c < 2; ++c) {
+                        s_pts[4 + c][Q.au] = U[c];
+                        s_pts[4 + c][Q.an] = Q.p_n;
+                        s_pts[4 + c][2] = 0.f;
+                    }
+                }
+            }
+        }
         __syncthreads();
         const int item = sm.item;
         if (item >= total_tiles)
             break;
-        // request of this tile: last r with tile_prefix[r] <= item
-        int lo_r = 0, hi_r = n_req - 1;
-        while (lo_r < hi_r) {
-            int mid = (lo_r + hi_r + 1) >> 1;
-            if (tile_prefix[mid] <= item)
-                lo_r = mid;
-            else
-                hi_r = mid - 1;
-        }
-        if (tid == 0)
-            s_req = reqs[lo_r];
-        __syncthreads();
         const DevRequest &R = s_req;
-        const int t = item - tile_prefix[lo_r];
+        const int t = sm.pad;
         const int per_layer = R.tiles_x * R.tiles_y;
         const int layer = t / per_layer;
         const int tt = t - layer * per_layer;
@@ -691,35 +746,6 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             continue;
         }
 
-        // hull of the tile's viewpoints and the target's patch centres
-        if (tid == 0) {
-            sm.n_planes = 0;
-            sm.count = 0;
-            s_next = 0;
-            const float X[2] = {R.x_coord[ix0], R.x_coord[ix1 - 1]};
-            const float Y[2] = {R.y_coord[iy0], R.y_coord[iy1 - 1]};
-            for (int c = 0; c < 4; ++c) {
-                s_pts[c][0] = X[c & 1];
-                s_pts[c][1] = Y[c >> 1];
-                s_pts[c][2] = (R.dims == 3) ? zq : 0.f;
-            }
-            if (R.dims == 3) {
-                const float U[2] = {R.u_min, R.u_max}, W[2] = {R.w_min, R.w_max};
-                for (int c = 0; c < 4; ++c) {
-                    s_pts[4 + c][R.au] = U[c & 1];
-                    s_pts[4 + c][R.aw] = W[c >> 1];
-                    s_pts[4 + c][R.an] = R.p_n;
-                }
-            } else {
-                const float U[2] = {R.u_min, R.u_max};
-                for (int c = 0; c < 2; ++c) {
-                    s_pts[4 + c][R.au] = U[c];
-                    s_pts[4 + c][R.an] = R.p_n;
-                    s_pts[4 + c][2] = 0.f;
-                }
-            }
-        }
-        __syncthreads();
         const int np = (R.dims == 3) ? 8 : 6;
         hull_planes(R.dims, s_pts, np, sm);
         __syncthreads();
@@ -862,8 +888,9 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                     }
                 continue;
             }
+            // the pyramid filter pays for its set-up only on long candidate lists
             Plane *pyr = s_pyr[warp];
-            const int npyr = pyramid_planes(R, qu, qn, qw, pyr);
+            const int npyr = count > kPyramidMinCount ? pyramid_planes(R, qu, qn, qw, pyr) : 0;
             float v;
             switch (R.k_rows) {
             case 1: v = sweep_k<1>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
