@@ -71,8 +71,21 @@ typedef enum {
 enum { VCM_AXIS_PX = 0, VCM_AXIS_NX = 1, VCM_AXIS_PY = 2, VCM_AXIS_NY = 3,
        VCM_AXIS_PZ = 4, VCM_AXIS_NZ = 5 };
 
-/* Request flags. */
-enum { VCM_EMIT_BITS = 1u };   /* also produce the per-patch occlusion bits */
+/* Request flags.
+ * VCM_EMIT_BITS: also produce the per-patch occlusion bits.
+ * VCM_STRICT:    a viewpoint keeps the whole target's measure only if no
+ *                patch is blocked, and gets 0 otherwise: the visible region
+ *                holds the points from which the target is completely
+ *                visible (Def. 3; end of Section III-B).
+ * VCM_VIEWER:    viewer-centric VCM (Section IV-B): `center` is the viewer,
+ *                `width` the size S of an object placed at every grid cell
+ *                facing the viewer; a cell's value is the object's visual
+ *                angle 2 atan(S / 2D) (2D, Eq. 1) or the solid angle of an
+ *                S x S square, 4 asin(S^2 / (S^2 + 4 D^2)) (3D), with D the
+ *                distance to the viewer, or 0 if the segment from the cell to
+ *                the viewer meets a box (or D = 0).  Axes, height and patch
+ *                counts are ignored; bits (one per cell) mark blocked cells. */
+enum { VCM_EMIT_BITS = 1u, VCM_STRICT = 2u, VCM_VIEWER = 4u };
 
 #define VCM_UNITS_PER_M 1024
 #define VCM_COORD_LIMIT_M 16384.0f

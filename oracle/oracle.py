@@ -33,7 +33,10 @@ class VoRequest(ctypes.Structure):
                 ("patches_u", ctypes.c_int32), ("patches_w", ctypes.c_int32),
                 ("grid_origin", ctypes.c_int64 * 2), ("grid_step", ctypes.c_int64 * 2),
                 ("grid_nx", ctypes.c_int32), ("grid_ny", ctypes.c_int32),
-                ("n_layers", ctypes.c_int32), ("layer_z", _i64p)]
+                ("n_layers", ctypes.c_int32), ("layer_z", _i64p), ("mode", ctypes.c_int32)]
+
+MODE_PARTIAL, MODE_STRICT, MODE_VIEWER = 0, 1, 2
+FLAG_STRICT, FLAG_VIEWER = 2, 4   # request flag bits that select the modes
 
 
 def build(force=False):
@@ -101,6 +104,8 @@ class _Pack:
         r.grid_nx, r.grid_ny = req["grid_nx"], req["grid_ny"]
         r.n_layers = len(req["layer_z"])
         r.layer_z = _p64(self.req_layers)
+        fl = int(req.get("flags", 0))
+        r.mode = MODE_VIEWER if fl & FLAG_VIEWER else (MODE_STRICT if fl & FLAG_STRICT else MODE_PARTIAL)
         self.s = None
         if scene is not None:
             self.lo = np.ascontiguousarray(scene.lo, dtype=np.int64)
@@ -153,7 +158,7 @@ def run(scene, req, indices=None, bits=False, threads=None):
         indices = np.arange(nvp, dtype=np.int64)
     indices = np.ascontiguousarray(indices, dtype=np.int64)
     n = indices.shape[0]
-    P = req["patches_u"] * req["patches_w"]
+    P = 1 if int(req.get("flags", 0)) & FLAG_VIEWER else req["patches_u"] * req["patches_w"]
     words = (P + 31) // 32
     v = np.zeros(n, np.float64)
     b = np.zeros((n, words), np.uint32) if bits else None

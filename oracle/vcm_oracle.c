@@ -29,10 +29,35 @@ static int64_t round_half_away(int64_t num, int64_t den)
 
 static int in_limit(int64_t x) { return x >= -COORD_LIMIT && x <= COORD_LIMIT; }
 
+static int vo_check_scene(const vo_scene *s, int dims)
+{
+    if (!s)
+        return 0;
+    if (s->dims != dims || s->n_boxes < 0 || (s->n_boxes > 0 && (!s->lo || !s->hi)))
+        return -1;
+    for (int64_t i = 0; i < s->n_boxes; ++i)
+        for (int k = 0; k < s->dims; ++k) {
+            int64_t lo = s->lo[3 * i + k], hi = s->hi[3 * i + k];
+            if (lo > hi || !in_limit(lo) || !in_limit(hi))
+                return -1;
+        }
+    return 0;
+}
+
 int vo_check(const vo_scene *s, const vo_request *r)
 {
     if (!r || (r->dims != 2 && r->dims != 3))
         return -1;
+    if (r->mode < VO_PARTIAL || r->mode > VO_VIEWER)
+        return -1;
+    if (r->mode == VO_VIEWER) {
+        if (r->width <= 0 || r->grid_nx < 1 || r->grid_ny < 1 || (r->dims == 3 && (r->n_layers < 1 || !r->layer_z)))
+            return -1;
+        for (int k = 0; k < 3; ++k)
+            if (!in_limit(r->center[k]))
+                return -1;
+        return vo_check_scene(s, r->dims);
+    }
     if (r->axis_u < 0 || r->axis_u > 5 || r->normal < 0 || r->normal > 5)
         return -1;
     if (r->dims == 3) {
@@ -50,17 +75,7 @@ int vo_check(const vo_scene *s, const vo_request *r)
     }
     if (r->patches_u < 1 || r->width <= 0 || r->grid_nx < 1 || r->grid_ny < 1)
         return -1;
-    if (s) {
-        if (s->dims != r->dims || s->n_boxes < 0 || (s->n_boxes > 0 && (!s->lo || !s->hi)))
-            return -1;
-        for (int64_t i = 0; i < s->n_boxes; ++i)
-            for (int k = 0; k < s->dims; ++k) {
-                int64_t lo = s->lo[3 * i + k], hi = s->hi[3 * i + k];
-                if (lo > hi || !in_limit(lo) || !in_limit(hi))
-                    return -1;
-            }
-    }
-    return 0;
+    return vo_check_scene(s, r->dims);
 }
 
 /* Patch centre: c + ((i + 1/2)/N - 1/2) * W along u (and likewise along w),
@@ -163,11 +178,31 @@ static int patch_blocked(const vo_scene *s, const int64_t q[3], const int64_t p[
     return 0;
 }
 
+/* Viewer-centric value of one grid cell (Section IV-B; VO_VIEWER above). */
+static double viewer_value(const vo_scene *s, const vo_request *r, const int64_t q[3], uint32_t *bits)
+{
+    int64_t v[3] = {r->center[0], r->center[1], (r->dims == 3) ? r->center[2] : 0};
+    int blocked = patch_blocked(s, q, v);
+    if (bits)
+        bits[0] = blocked ? 1u : 0u;
+    double dx = (double)(q[0] - v[0]) / UNITS_PER_M, dy = (double)(q[1] - v[1]) / UNITS_PER_M;
+    double dz = (double)(q[2] - v[2]) / UNITS_PER_M;
+    double D = sqrt(dx * dx + dy * dy + dz * dz);
+    if (blocked || !(D > 0.0))
+        return 0.0;
+    double S = (double)r->width / UNITS_PER_M;
+    if (r->dims == 2)
+        return 2.0 * atan(S / (2.0 * D));              /* Eq. 1 */
+    return 4.0 * asin(S * S / (S * S + 4.0 * D * D));  /* S x S square facing the viewer */
+}
+
 double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint32_t *bits)
 {
     int64_t q[3];
     if (vo_viewpoint(r, index, q) != 0)
         return NAN;
+    if (r->mode == VO_VIEWER)
+        return viewer_value(s, r, q, bits);
     int64_t P = (int64_t)r->patches_u * ((r->dims == 3) ? r->patches_w : 1);
     int64_t *pc = (int64_t *)malloc(sizeof(int64_t) * 3 * P);
     if (!pc || vo_patch_centres(r, pc) != 0) {
@@ -181,13 +216,15 @@ double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint
     double sn = (double)axis_sign(r->normal);
     double measure = vo_patch_measure(r);
     double sum = 0.0, comp = 0.0;   /* Neumaier running sum and compensation */
+    int any_blocked = 0;
     for (int64_t j = 0; j < P; ++j) {
         const int64_t *p = pc + 3 * j;
         /* cos(theta) * |r| = n . (q - p): positive in front of the target */
         double cos_r = sn * (double)(q[an] - p[an]) / UNITS_PER_M;
         int blocked = 0;
-        if (bits || cos_r > 0.0)
+        if (bits || cos_r > 0.0 || r->mode == VO_STRICT)
             blocked = patch_blocked(s, q, p);
+        any_blocked |= blocked;
         if (bits && blocked)
             bits[j >> 5] |= 1u << (j & 31);
         if (blocked || !(cos_r > 0.0))
@@ -209,6 +246,8 @@ double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint
         sum = t;
     }
     free(pc);
+    if (r->mode == VO_STRICT && any_blocked)
+        return 0.0;   /* not completely visible: obstructed region */
     return sum + comp;
 }
 
@@ -242,7 +281,7 @@ int vo_run(const vo_scene *s, const vo_request *r, const int64_t *indices, int64
     for (int64_t i = 0; i < n; ++i)
         if (indices[i] < 0 || indices[i] >= nvp)
             return -1;
-    int64_t P = (int64_t)r->patches_u * ((r->dims == 3) ? r->patches_w : 1);
+    int64_t P = (r->mode == VO_VIEWER) ? 1 : (int64_t)r->patches_u * ((r->dims == 3) ? r->patches_w : 1);
     if (threads < 1)
         threads = 1;
     if (threads > 256)

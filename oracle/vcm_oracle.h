@@ -52,7 +52,23 @@ typedef struct {
     int32_t grid_nx, grid_ny;
     int32_t n_layers;
     const int64_t *layer_z;           /* [n_layers]; ignored in 2D */
+    int32_t mode;                     /* VO_PARTIAL, VO_STRICT or VO_VIEWER */
 } vo_request;
+
+/* Modes.
+ * VO_PARTIAL: the sum over the unblocked patches (above).
+ * VO_STRICT:  the viewpoint keeps the whole target's measure only if no
+ *             patch is blocked, else 0 (the visible region holds the points
+ *             from which the target is completely visible, Def. 3 and the
+ *             end of Section III-B).
+ * VO_VIEWER:  viewer-centric VCM (Section IV-B): `center` is the viewer and
+ *             `width` the size S of an object placed at each grid cell and
+ *             facing the viewer; a cell's value is the object's visual angle
+ *             2 atan(S / 2D) (2D, Eq. 1) or the solid angle of an S x S
+ *             square 4 asin(S^2 / (S^2 + 4 D^2)) (3D), D the distance to the
+ *             viewer, and 0 if the segment to the viewer is blocked or D = 0.
+ *             One occlusion bit per cell. */
+enum { VO_PARTIAL = 0, VO_STRICT = 1, VO_VIEWER = 2 };
 
 /* 0 on success, -1 on an invalid request. */
 int vo_check(const vo_scene *s, const vo_request *r);

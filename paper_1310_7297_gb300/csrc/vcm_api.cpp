@@ -120,6 +120,34 @@ int perm_index(int a0, int a1, int a2)
     return -1;
 }
 
+vcm_status canonicalise_grid(const vcm_request *r, Canon &c);
+
+// Viewer-centric request: the viewer is a one-point "target" in the world
+// frame (u = x, n = y, w = z), the object size S is kept in `measure`.
+vcm_status canonicalise_viewer(const vcm_request *r, Canon &c)
+{
+    c.au = 0;
+    c.an = 1;
+    c.aw = 2;
+    c.perm = 0;
+    c.sn = 1.f;
+    c.nu = c.nw = c.P = c.words = 1;
+    int64_t cu[3] = {0, 0, 0};
+    for (int k = 0; k < c.dims; ++k)
+        if (!to_units(r->center[k], cu[k]))
+            return fail(VCM_E_ARG, "viewer center[%d] is not a finite lattice value within 16384 m", k);
+    int64_t S = 0;
+    if (!to_units(r->width, S) || S <= 0)
+        return fail(VCM_E_ARG, "width (object size S) must be a positive lattice value");
+    c.u_coord.assign(1, units_to_float(cu[0]));
+    c.w_coord.assign(1, units_to_float(cu[2]));
+    c.p_n = units_to_float(cu[1]);
+    c.u_min = c.u_max = c.u_coord[0];
+    c.w_min = c.w_max = c.w_coord[0];
+    c.measure = units_to_float(S);
+    return canonicalise_grid(r, c);
+}
+
 vcm_status canonicalise(const vcm_request *r, Canon &c)
 {
     if (!r)
@@ -127,11 +155,15 @@ vcm_status canonicalise(const vcm_request *r, Canon &c)
     if (r->dims != 2 && r->dims != 3)
         return fail(VCM_E_ARG, "dims must be 2 or 3 (got %d)", r->dims);
     c.dims = r->dims;
+    if (r->flags & ~(uint32_t)(VCM_EMIT_BITS | VCM_STRICT | VCM_VIEWER))
+        return fail(VCM_E_ARG, "unknown flag bits 0x%x", r->flags);
+    if ((r->flags & VCM_STRICT) && (r->flags & VCM_VIEWER))
+        return fail(VCM_E_ARG, "VCM_STRICT and VCM_VIEWER exclude each other");
+    c.flags = r->flags;
+    if (r->flags & VCM_VIEWER)
+        return canonicalise_viewer(r, c);
     if (r->axis_u < 0 || r->axis_u > 5 || r->normal < 0 || r->normal > 5)
         return fail(VCM_E_ARG, "axis codes must be 0..5");
-    if (r->flags & ~(uint32_t)VCM_EMIT_BITS)
-        return fail(VCM_E_ARG, "unknown flag bits 0x%x", r->flags);
-    c.flags = r->flags;
     c.au = r->axis_u >> 1;
     c.an = r->normal >> 1;
     c.sn = (r->normal & 1) ? -1.f : 1.f;
@@ -206,7 +238,12 @@ vcm_status canonicalise(const vcm_request *r, Canon &c)
         const double lu = (double)W / kUnitsPerM / c.nu;
         c.measure = (float)(c.dims == 3 ? lu * ((double)H / kUnitsPerM / c.nw) : lu);
     }
-    // viewpoint grid
+    return canonicalise_grid(r, c);
+}
+
+// The viewpoint grid, layers, colour levels and v_ref of a request.
+vcm_status canonicalise_grid(const vcm_request *r, Canon &c)
+{
     if (r->grid_nx < 1 || r->grid_ny < 1 || r->grid_nx > VCM_MAX_GRID_SIDE || r->grid_ny > VCM_MAX_GRID_SIDE)
         return fail(VCM_E_ARG, "grid_nx and grid_ny must be 1..%u", VCM_MAX_GRID_SIDE);
     c.nx = (int)r->grid_nx;
@@ -390,6 +427,7 @@ struct vcm_ctx {
     uint32_t n_boxes = 0;
     std::vector<float> h_lo, h_hi;   // n x 3
     float *d_lo = nullptr, *d_hi = nullptr;
+    size_t lo_cap = 0, idx_box_cap = 0, idx_cell_cap = 0;   // allocated capacities (boxes, cells + 1)
     bool built = false;
     float4 *d_perm[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int *d_cell_start = nullptr, *d_cell_of = nullptr, *d_count = nullptr, *d_cursor = nullptr, *d_order = nullptr;
@@ -735,6 +773,7 @@ void free_scene(vcm_ctx *ctx)
     ctx->d_cell_start = ctx->d_cell_of = ctx->d_count = ctx->d_cursor = ctx->d_order = nullptr;
     ctx->d_cell_lo = ctx->d_cell_hi = nullptr;
     ctx->d_overhang = nullptr;
+    ctx->lo_cap = ctx->idx_box_cap = ctx->idx_cell_cap = 0;
     ctx->built = false;
 }
 
@@ -1124,15 +1163,23 @@ vcm_status vcm_scene_load_mem(vcm_ctx *ctx, const float *lo, const float *hi, ui
         std::lock_guard<std::mutex> g(ctx->mu);
         if (!scheduler_idle(ctx))
             return fail(VCM_E_STATE, "requests are still queued or running");
+        // work still reading the old scene must finish before it is replaced
         CUDA_TRY(cudaDeviceSynchronize());
-        free_scene(ctx);
+        ctx->built = false;
         ctx->dims = dims;
         ctx->n_boxes = n_boxes;
         ctx->h_lo.swap(L);
         ctx->h_hi.swap(H);
-        const size_t bytes = std::max<size_t>(1, (size_t)n_boxes * 3) * sizeof(float);
-        CUDA_TRY(cudaMalloc(&ctx->d_lo, bytes));
-        CUDA_TRY(cudaMalloc(&ctx->d_hi, bytes));
+        const size_t nb = std::max<uint32_t>(n_boxes, 1);
+        if (nb > ctx->lo_cap) {   // buffers are kept and reused while large enough
+            cudaFree(ctx->d_lo);
+            cudaFree(ctx->d_hi);
+            ctx->d_lo = ctx->d_hi = nullptr;
+            ctx->lo_cap = 0;
+            CUDA_TRY(cudaMalloc(&ctx->d_lo, nb * 3 * sizeof(float)));
+            CUDA_TRY(cudaMalloc(&ctx->d_hi, nb * 3 * sizeof(float)));
+            ctx->lo_cap = nb;
+        }
         if (n_boxes) {
             CUDA_TRY(cudaMemcpy(ctx->d_lo, ctx->h_lo.data(), (size_t)n_boxes * 12, cudaMemcpyHostToDevice));
             CUDA_TRY(cudaMemcpy(ctx->d_hi, ctx->h_hi.data(), (size_t)n_boxes * 12, cudaMemcpyHostToDevice));
@@ -1231,24 +1278,43 @@ vcm_status vcm_build(vcm_ctx *ctx, float grid_cell_m)
             cell *= 1.5;
         const int gnx = (int)std::ceil(w / cell) + 1, gny = (int)std::ceil(h / cell) + 1;
         const int n_cells = gnx * gny;
-        for (auto &p : ctx->d_perm) {
-            cudaFree(p);
-            p = nullptr;
-        }
-        cudaFree(ctx->d_cell_start); cudaFree(ctx->d_cell_of); cudaFree(ctx->d_count);
-        cudaFree(ctx->d_cursor); cudaFree(ctx->d_order); cudaFree(ctx->d_cell_lo); cudaFree(ctx->d_cell_hi);
-        cudaFree(ctx->d_overhang);
+        // work still reading the old index must finish before it is rebuilt
+        CUDA_TRY(cudaDeviceSynchronize());
+        ctx->built = false;
         const size_t nb = std::max<uint32_t>(n, 1);
-        for (auto &p : ctx->d_perm)
-            CUDA_TRY(cudaMalloc(&p, nb * 2 * sizeof(float4)));
-        CUDA_TRY(cudaMalloc(&ctx->d_cell_start, sizeof(int) * (n_cells + 1)));
-        CUDA_TRY(cudaMalloc(&ctx->d_cell_of, sizeof(int) * nb));
-        CUDA_TRY(cudaMalloc(&ctx->d_count, sizeof(int) * n_cells));
-        CUDA_TRY(cudaMalloc(&ctx->d_cursor, sizeof(int) * n_cells));
-        CUDA_TRY(cudaMalloc(&ctx->d_order, sizeof(int) * nb));
-        CUDA_TRY(cudaMalloc(&ctx->d_cell_lo, sizeof(float4) * n_cells));
-        CUDA_TRY(cudaMalloc(&ctx->d_cell_hi, sizeof(float4) * n_cells));
-        CUDA_TRY(cudaMalloc(&ctx->d_overhang, sizeof(unsigned)));
+        if (nb > ctx->idx_box_cap) {   // index buffers are reused while large enough
+            for (auto &p : ctx->d_perm) {
+                cudaFree(p);
+                p = nullptr;
+            }
+            cudaFree(ctx->d_cell_of);
+            cudaFree(ctx->d_order);
+            ctx->d_cell_of = ctx->d_order = nullptr;
+            ctx->idx_box_cap = 0;
+            for (auto &p : ctx->d_perm)
+                CUDA_TRY(cudaMalloc(&p, nb * 2 * sizeof(float4)));
+            CUDA_TRY(cudaMalloc(&ctx->d_cell_of, sizeof(int) * nb));
+            CUDA_TRY(cudaMalloc(&ctx->d_order, sizeof(int) * nb));
+            ctx->idx_box_cap = nb;
+        }
+        if ((size_t)n_cells + 1 > ctx->idx_cell_cap) {
+            cudaFree(ctx->d_cell_start);
+            cudaFree(ctx->d_count);
+            cudaFree(ctx->d_cursor);
+            cudaFree(ctx->d_cell_lo);
+            cudaFree(ctx->d_cell_hi);
+            ctx->d_cell_start = ctx->d_count = ctx->d_cursor = nullptr;
+            ctx->d_cell_lo = ctx->d_cell_hi = nullptr;
+            ctx->idx_cell_cap = 0;
+            CUDA_TRY(cudaMalloc(&ctx->d_cell_start, sizeof(int) * (n_cells + 1)));
+            CUDA_TRY(cudaMalloc(&ctx->d_count, sizeof(int) * n_cells));
+            CUDA_TRY(cudaMalloc(&ctx->d_cursor, sizeof(int) * n_cells));
+            CUDA_TRY(cudaMalloc(&ctx->d_cell_lo, sizeof(float4) * n_cells));
+            CUDA_TRY(cudaMalloc(&ctx->d_cell_hi, sizeof(float4) * n_cells));
+            ctx->idx_cell_cap = (size_t)n_cells + 1;
+        }
+        if (!ctx->d_overhang)
+            CUDA_TRY(cudaMalloc(&ctx->d_overhang, sizeof(unsigned)));
         CUDA_TRY(launch_grid_build(ctx->d_lo, ctx->d_hi, (int)n, ctx->dims, (float)x0, (float)y0, (float)cell, gnx,
                                    gny, ctx->d_cell_of, ctx->d_count, ctx->d_cursor, ctx->d_order,
                                    ctx->d_cell_start, ctx->d_perm, ctx->d_cell_lo, ctx->d_cell_hi,
@@ -1493,9 +1559,11 @@ vcm_status vcm_set_tune(vcm_ctx *ctx, const vcm_tune *tune)
         ctx->forced = false;
         return VCM_OK;
     }
-    if (tune->tile_x > 256 || tune->tile_y < 1 || tune->tile_y > 256 || tune->patch_k > 16 ||
+    if (tune->tile_x > 256 || tune->tile_y < 1 || tune->tile_y > 256 ||
+        tune->tile_x * tune->tile_y > (uint32_t)kMaxTileViewpoints || tune->patch_k > 16 ||
         tune->box_cap < 32 || tune->box_cap > 5000)
-        return fail(VCM_E_ARG, "tile sides 1..256, patch_k 0..16 (rows per pass are capped at 8), box_cap 32..5000");
+        return fail(VCM_E_ARG, "tile sides 1..256 with at most %d viewpoints per tile, patch_k 0..16 (rows per "
+                    "pass are capped at 8), box_cap 32..5000", kMaxTileViewpoints);
     ctx->forced = true;
     ctx->forced_tune = *tune;
     return VCM_OK;

@@ -16,6 +16,7 @@ constexpr int kMaxPlanes = 32;            // separating planes kept per tile hul
 constexpr float kBand = 1e-6f;            // FP32 slab margin re-decided in FP64
 constexpr int kMaxBoxCap = 5000;          // candidate boxes a tile stages in shared memory
 constexpr int kPyramidMinCount = 64;      // candidate lists longer than this get the pyramid filter
+constexpr int kMaxTileViewpoints = 1024;  // viewpoints in one tile (tile_x * tile_y)
 
 inline size_t tiles_smem_bytes(int box_cap) { return (size_t)box_cap * (32 + 4); }
 

@@ -468,10 +468,14 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
     const bool sgn_n = dn >= 0.f;
     const bool sgn_w_uni = qw <= R.w_min;    // all rows at dw >= 0 (used when !MIXED)
     const bool want_bits = (R.flags & VCM_EMIT_BITS) && R.bits_out;
+    // strict: any blocked patch zeroes the viewpoint, so the first one ends it
+    const bool strict = (R.flags & VCM_STRICT) != 0;
+    const bool strict_exit = strict && !want_bits;
+    bool strict_fail = false;
     const float *__restrict__ w_coord = R.w_coord;
     float sum = 0.f, comp = 0.f;
 
-    for (int cp = 0; cp < R.col_passes; ++cp) {
+    for (int cp = 0; cp < R.col_passes && !(strict_exit && strict_fail); ++cp) {
         const int iu = cp * nuc + c_in;
         const bool col_ok = lane_ok && iu < R.nu;
         const float pu = R.u_coord[col_ok ? iu : 0];
@@ -481,7 +485,7 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
         const float ru = qu - pu, rn = qn - R.p_n;
         const float col_d2 = fmaf(ru, ru, rn * rn);
         const float m_s = R.measure * (R.sn * rn);   // measure x |r| cos(theta)
-        for (int rp = 0; rp < R.row_passes; ++rp) {
+        for (int rp = 0; rp < R.row_passes && !(strict_exit && strict_fail); ++rp) {
             float inv_w[K], clampv[K];
             unsigned valid = 0, sgnw = 0;
 #pragma unroll
@@ -578,15 +582,17 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                         }
                     }
                 }
-                if (__all_sync(kFull, alive == 0)) {
+                if (__all_sync(kFull, alive == 0) || (strict_exit && __any_sync(kFull, alive != valid))) {
                     done = true;
                     break;
                 }
               }
             }
             tests += (unsigned long long)nb * K;
+            if (strict)
+                strict_fail |= __any_sync(kFull, alive != valid);
             // visible measure of the unblocked rows, and the blocked bits
-            if (want_bits || __any_sync(kFull, alive != 0)) {
+            if (want_bits || (!strict_fail && __any_sync(kFull, alive != 0))) {
 #pragma unroll
                 for (int m = 0; m < K; ++m) {
                     if (!((valid >> m) & 1u))
@@ -626,7 +632,54 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
         v += __shfl_xor_sync(kFull, v, off);
-    return v;
+    return strict_fail ? 0.f : v;
+}
+
+// Viewer-centric cell (VCM_VIEWER): one segment from the cell q to the
+// viewer p (world frame) against the candidate boxes, nearest first; the
+// cell's value is the visual angle (2D, Eq. 1) or solid angle (3D) of an
+// object of size S at distance D facing the viewer, 0 when blocked or D = 0.
+__device__ __forceinline__ float viewer_cell(const DevRequest &R, const float4 *__restrict__ sbox, int n_smem,
+                                             const int *__restrict__ spill, int count,
+                                             const float4 *__restrict__ gbox, float qx, float qy, float qz,
+                                             bool &blocked, unsigned long long &tests, unsigned &rechecks)
+{
+    const float px = R.u_min, py = R.p_n, pz = R.w_min;
+    const float dx = px - qx, dy = py - qy, dz = pz - qz;
+    const float ix = rcp_approx(dx), iy = rcp_approx(dy), iz = rcp_approx(dz);
+    blocked = false;
+    for (int i = 0; i < count && !blocked; ++i) {
+        float4 lo, hi;
+        if (i < n_smem) {
+            lo = sbox[2 * i];
+            hi = sbox[2 * i + 1];
+        } else {
+            const int s = spill[i - n_smem];
+            lo = __ldg(&gbox[2 * s]);
+            hi = __ldg(&gbox[2 * s + 1]);
+        }
+        ++tests;
+        const float ax = lo.x - qx, bx = hi.x - qx, ay = lo.y - qy, by = hi.y - qy, az = lo.z - qz, bz = hi.z - qz;
+        const float enter = fmaxf(fmaxf((dx >= 0.f ? ax : bx) * ix, (dy >= 0.f ? ay : by) * iy),
+                                  fmaxf((dz >= 0.f ? az : bz) * iz, 0.f));
+        const float exit_ = fminf(fminf((dx >= 0.f ? bx : ax) * ix, (dy >= 0.f ? by : ay) * iy),
+                                  fminf((dz >= 0.f ? bz : az) * iz, 1.f));
+        const float mv = exit_ - enter;
+        if (mv >= -kBand) {
+            blocked = mv > kBand;
+            if (!blocked) {
+                ++rechecks;
+                blocked = exact_hit(qx, qy, qz, px, py, pz, lo, hi);
+            }
+        }
+    }
+    const float D = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    if (blocked || !(D > 0.f))
+        return 0.f;
+    const float S = R.measure;
+    if (R.dims == 2)
+        return 2.f * atanf(S / (2.f * D));
+    return 4.f * asinf(S * S / fmaf(4.f * D, D, S * S));
 }
 
 template <int K>
@@ -655,9 +708,12 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
     __shared__ DevRequest s_req;
     __shared__ int s_next;
     __shared__ Plane s_pyr[kWarps][6];
+    __shared__ int s_req_idx;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int *spill = spill_all + (size_t)blockIdx.x * sc.n_boxes;
+    if (tid == 0)
+        s_req_idx = -1;
 
     for (;;) {
         // thread 0 takes the next tile, copies its request and lays out the
@@ -675,7 +731,10 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                     else
                         hi_r = mid - 1;
                 }
-                s_req = reqs[lo_r];
+                if (lo_r != s_req_idx) {   // consecutive tiles mostly share a request
+                    s_req = reqs[lo_r];
+                    s_req_idx = lo_r;
+                }
                 sm.pad = it - tile_prefix[lo_r];   // tile index within its request
                 const DevRequest &Q = s_req;
                 const int t0 = sm.pad, pl = Q.tiles_x * Q.tiles_y;
@@ -736,7 +795,8 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         } else {
             qn_lo = R.y_coord[iy0]; qn_hi = R.y_coord[iy1 - 1];
         }
-        const bool any_front = R.sn > 0.f ? (qn_hi - R.p_n > 0.f) : (R.p_n - qn_lo > 0.f);
+        const bool viewer = (R.flags & VCM_VIEWER) != 0;
+        const bool any_front = viewer || (R.sn > 0.f ? (qn_hi - R.p_n > 0.f) : (R.p_n - qn_lo > 0.f));
         if (!any_front && !want_bits) {
             for (int i = tid; i < tn; i += kThreads) {
                 const int ix = ix0 + i % tw, iy = iy0 + i / tw;
@@ -856,7 +916,21 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         unsigned long long tests = 0, corner_tests = 0;
         unsigned rechecks = 0, shortcuts = 0;
         float vmax = 0.f;
-        for (;;) {
+        if (viewer) {
+            // viewer-centric: threads take cells, one segment each
+            for (int vi = tid; vi < tn; vi += kThreads) {
+                const int ix = ix0 + vi % tw, iy = iy0 + vi / tw;
+                const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
+                bool blocked;
+                const float v = viewer_cell(R, s_box, n_smem, spill, count, gbox, R.x_coord[ix], R.y_coord[iy],
+                                            R.dims == 3 ? zq : 0.f, blocked, tests, rechecks);
+                R.v_out[vp] = v;
+                if (want_bits)
+                    R.bits_out[vp] = blocked ? 1u : 0u;
+                vmax = fmaxf(vmax, v);
+            }
+        }
+        for (; !viewer;) {
             int vi = 0;
             if (lane == 0)
                 vi = atomicAdd(&s_next, 1);
@@ -905,10 +979,14 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             vmax = fmaxf(vmax, v);
         }
         // per-tile counters
+        for (int off = 16; off > 0; off >>= 1) {
+            tests += __shfl_xor_sync(kFull, tests, off);
+            vmax = fmaxf(vmax, __shfl_xor_sync(kFull, vmax, off));
+        }
         if (lane == 0) {
             atomicMax(&R.stats->vmax_bits, __float_as_uint(vmax));
             if (tests)
-                atomicAdd(&R.stats->slab_tests, tests * 32ull);
+                atomicAdd(&R.stats->slab_tests, tests);
             if (corner_tests)
                 atomicAdd(&R.stats->corner_tests, corner_tests);
             if (shortcuts)

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libvcm.so")
 VCM_OK, VCM_PENDING = 0, 1
 VCM_E_ARG, VCM_E_IO, VCM_E_NOMEM, VCM_E_CUDA = -1, -2, -3, -4
 VCM_E_TIMEOUT, VCM_E_CANCELLED, VCM_E_STATE = -5, -6, -7
-VCM_EMIT_BITS = 1
+VCM_EMIT_BITS, VCM_STRICT, VCM_VIEWER = 1, 2, 4
 STATUS_NAMES = {0: "VCM_OK", 1: "VCM_PENDING", -1: "VCM_E_ARG", -2: "VCM_E_IO", -3: "VCM_E_NOMEM",
                 -4: "VCM_E_CUDA", -5: "VCM_E_TIMEOUT", -6: "VCM_E_CANCELLED", -7: "VCM_E_STATE"}
 UNITS_PER_M = 1024
@@ -145,6 +145,8 @@ def n_viewpoints(d):
 
 
 def words(d):
+    if d.get("flags", 0) & VCM_VIEWER:
+        return 1   # one bit per cell
     return (d["patches_u"] * (d["patches_w"] if d["dims"] == 3 else 1) + 31) // 32
 
 

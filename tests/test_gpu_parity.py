@@ -385,3 +385,52 @@ def test_workload_batched_full_mix_sampled(ctx):
         ov, ob = O.run(sc, r, indices=idx, bits=True)
         compare_bits(ob, gb, "batched request %d" % k)
         compare_v(ov, gv[idx], "batched request %d" % k)
+
+
+# ---------------------------------------------------------------------------
+# strict (completely visible) and viewer-centric modes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_strict_mode(ctx, which):
+    from paper_1310_7297_gb300 import VCM_STRICT
+
+    if which == "2d":
+        sc, req = synth.workload_2d(seed=6)
+    else:
+        sc, req = synth.workload_3d(seed=43, grid=40, layers=3, patches=(16, 8), n_boxes=300, half_m=400.0,
+                                    n_components=5, sigma_m=(60.0, 150.0))
+    load(ctx, sc)
+    r = dict(req, flags=VCM_STRICT)
+    gv, gb, st, err, mism = full_parity(ctx, sc, r)
+    vp = O.run(sc, req)
+    assert (gv > 0).sum() > 20 and ((vp > 0) & (gv == 0)).sum() > 20   # some partly visible cells drop out
+    # without bits (the any-blocked early exit) the values are the same
+    gv2, _, _, _ = gpu_run(ctx, r, bits=False)
+    assert np.array_equal(gv2, gv)
+
+
+@pytest.mark.parametrize("which", ["2d", "3d", "3d_inside"])
+def test_viewer_mode(ctx, which):
+    from paper_1310_7297_gb300 import VCM_VIEWER
+    from synth import make_request
+
+    if which == "2d":
+        sc, _ = synth.workload_2d(seed=7)
+        r = make_request(2, (37.0, -12.5), 0, 2, 2.0, 1, (-500.0, -500.0), (1000 / 96, 1000 / 96), (96, 96),
+                         color_levels=8, flags=VCM_VIEWER)
+    else:
+        sc, _ = synth.workload_3d(seed=44, grid=8, n_boxes=600, half_m=400.0, n_components=5,
+                                  sigma_m=(60.0, 150.0))
+        viewer = (12.0, -30.0, 25.0)
+        if which == "3d_inside":   # a viewer inside a box sees nothing
+            b = sc.lo[0] + (sc.hi[0] - sc.lo[0]) // 2
+            viewer = tuple(float(x) / 1024 for x in b)
+        r = make_request(3, viewer, 0, 2, 1.0, 1, (-400.0, -400.0), (800 / 64, 800 / 64), (64, 64),
+                         layers_m=(1.7, 21.7, 61.7), axis_w=4, height_m=1.0, color_levels=16, flags=VCM_VIEWER)
+    load(ctx, sc)
+    gv, gb, st, err, mism = full_parity(ctx, sc, r)
+    if which == "3d_inside":
+        assert (gv == 0).all() and gb.all()
+    else:
+        assert (gv > 0).sum() > 200 and gb.any()

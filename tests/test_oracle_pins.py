@@ -384,3 +384,72 @@ def test_quantiser_properties():
     assert set(cc.tolist()) == set(range(1, L))
     assert O.quantise(np.zeros(5), 0.0, L).tolist() == [0] * 5
     assert O.vmax(np.array([0.0, 3.0, 1.0])) == 3.0
+
+
+# ---------------------------------------------------------------------------
+# strict and viewer-centric modes
+# ---------------------------------------------------------------------------
+
+STRICT, VIEWER = 2, 4
+
+
+def test_strict_mode_is_all_or_nothing():
+    """Def. 3: the visible region holds the viewpoints that see every patch;
+    there the strict value equals the unobstructed one, elsewhere it is 0."""
+    import synth
+
+    sc, r = synth.workload_3d(seed=41, grid=20, layers=3, patches=(8, 4), n_boxes=80, half_m=250.0,
+                              n_components=4, sigma_m=(40.0, 100.0))
+    vp, bp = O.run(sc, r, bits=True, threads=4)
+    vs = O.run(sc, dict(r, flags=STRICT), threads=4)
+    v0 = O.run(scene(3, []), r, threads=4)
+    none_blocked = ~bp.astype(bool).any(axis=1)
+    assert np.array_equal(vs[none_blocked], v0[none_blocked])
+    assert np.all(vs[~none_blocked] == 0.0)
+    assert np.array_equal(vs[none_blocked], vp[none_blocked])
+    assert np.all(vs <= vp + 1e-15) and (vs > 0).any() and ((vp > 0) & (vs == 0)).any()
+
+
+def _viewer_req(dims, viewer, S, origin, step, n, layers=(0,)):
+    from helpers import req2, req3
+
+    if dims == 2:
+        r = req2((viewer[0], viewer[1]), width=S, origin=origin, step=step, n=n)
+    else:
+        r = req3(tuple(viewer), width=S, origin=origin, step=step, n=n, layers=layers)
+    r["flags"] = VIEWER
+    return r
+
+
+def test_viewer_mode_reproduces_the_paper_example_exactly():
+    """Section IV-B with Eq. 1: an object of S = 300 m at D = 400 m from the
+    viewer subtends 41.11 degrees (the worked example of Section II-B.1)."""
+    g = read_golden("paper_visual_angle.txt")
+    S, D = int(g["S_m"]), int(g["D_m"])
+    r = _viewer_req(2, (0, 0), S * U, (-1, D * U - 1), (2, 2), (1, 1))
+    v = O.run(scene(2, []), r)[0]
+    assert v == pytest.approx(2.0 * math.atan(S / (2.0 * D)), rel=1e-14)
+    assert round(math.degrees(v), int(g["printed_decimals"])) == pytest.approx(g["V_deg"], abs=1e-9)
+
+
+def test_viewer_mode_3d_square_solid_angle_and_blocking():
+    """3D cells: the solid angle of an S x S square facing the viewer, checked
+    against the corner-decomposition closed form; a wall zeroes the cells
+    behind it and sets their bits, as the separating-axis brute force says."""
+    S = 4 * U
+    r = _viewer_req(3, (0, 0, 10 * U), S, (-40 * U, 5 * U), (10 * U, 10 * U), (8, 6), layers=(2 * U, 10 * U))
+    v0 = O.run(scene(3, []), r)
+    for idx in (0, 7, 20, 47, 60):
+        q = O.viewpoint(r, idx) / U
+        D = math.dist(q, (0.0, 0.0, 10.0))
+        # square of side S at distance D, seen on its axis: rectangle formula
+        ref = _rect_solid_angle((0.0, D, 0.0), (0.0, 0.0, 0.0), S / U, S / U)
+        assert v0[idx] == pytest.approx(ref, rel=1e-12)
+    wall = scene(3, [((-15 * U, 20 * U, 0), (15 * U, 21 * U, 30 * U))])
+    v, b = O.run(wall, r, bits=True)
+    for idx in range(v.shape[0]):
+        q = tuple(int(x) for x in O.viewpoint(r, idx))
+        hit = brute.segment_hits_box_sat(3, q, (0, 0, 10 * U), wall.lo[0], wall.hi[0])
+        assert bool(b[idx, 0]) == hit
+        assert (v[idx] == 0.0) == hit
+    assert b.any() and not b.all()
