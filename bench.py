@@ -371,7 +371,11 @@ def run_batched(args):
     ctx.load_scene(scene)
     ctx.vcm_build(50.0)
     t0 = time.perf_counter()
-    samples = sorted(reqs, key=lambda r: n_viewpoints(r))[: max(4, len(reqs) // 16)]
+    # one median-sized request of each patch-count class
+    classes = {}
+    for r in reqs:
+        classes.setdefault((r["patches_u"], r["patches_w"]), []).append(r)
+    samples = [sorted(v, key=n_viewpoints)[len(v) // 2] for v in classes.values()]
     tuned = ctx.vcm_autotune(samples)
     tune_s = time.perf_counter() - t0
     vs, cs, st = _alloc_outputs(torch, dev, reqs)
@@ -506,6 +510,56 @@ def run_serve(args):
     ctx.close()
 
 
+def run_large(args):
+    """The large scene at full size: 100,000 boxes over 10 km x 10 km, one
+    40 m x 20 m target split 64 x 32, 2048 x 2048 x 8 viewpoints, 50 m grid
+    index.  Same timing rules as the default step."""
+    import torch
+
+    import synth
+    from paper_1310_7297_gb300 import Context, stats_from_tensor
+    from paper_1310_7297_gb300 import build as B
+    from paper_1310_7297_gb300.vcm import STATS_BYTES
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    scene, req = synth.workload_3d_large()
+    n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
+    seg = n_vp * req["patches_u"] * req["patches_w"]
+    ctx = Context(0)
+    ctx.load_scene(scene)
+    ctx.vcm_build(50.0)
+    stream = torch.cuda.current_stream(dev)
+    v = torch.empty(n_vp, dtype=torch.float32, device=dev)
+    c = torch.empty(n_vp, dtype=torch.uint8, device=dev)
+    st = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(1, args.warmup)):
+        ctx.vcm_compute(req, v.data_ptr(), c.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.vcm_compute(req, v.data_ptr(), c.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    stats = stats_from_tensor(st)
+    out = {"mode": "large", "metric": METRIC, "unit": UNIT, "boxes": scene.n, "viewpoints": n_vp,
+           "patches": [req["patches_u"], req["patches_w"]], "segments": seg, "ms_per_step": float(np.mean(ms)),
+           "value": seg / (float(np.mean(ms)) / 1e3), "cells_per_s": n_vp / (float(np.mean(ms)) / 1e3),
+           "stats": {k: stats[k] for k in ("slab_tests", "corner_tests", "shortcut_viewpoints", "rechecked",
+                                           "boxes_listed")},
+           "nonzero_cells": int((v > 0).sum().item())}
+    if not args.no_cpu_baseline:
+        r = oracle_rate(scene, req, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                               "sample": "%d random viewpoints, %.1f s" % (r["viewpoints"], r["seconds"])}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,8 +568,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "batched", "serve"], default="step",
-                    help="step: the timed VCM step (default); batched / serve: the batching and serving runs")
+    ap.add_argument("--mode", choices=["step", "batched", "serve", "large"], default="step",
+                    help="step: the timed VCM step (default); batched / serve: the batching and serving runs; "
+                         "large: the 100,000-box scene at full size")
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=400)
@@ -530,6 +585,8 @@ def main():
         run_batched(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "large":
+        run_large(args)
     else:
         run_gpu(args)
 

@@ -1772,11 +1772,33 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
         double best_ms[kTuneClasses];
         vcm_tune best[kTuneClasses];
         bool seen[kTuneClasses] = {false};
-        for (int c = 0; c < kTuneClasses; ++c) {
-            best_ms[c] = 1e300;
-            best[c] = default_tune();
-        }
         std::lock_guard<std::mutex> g(ctx->mu);
+        // Time one shape on a class's samples: best of three launches each,
+        // summed over the samples (one warm-up launch first).
+        auto time_shape = [&](const std::vector<const Canon *> &mine, const vcm_tune &t, double &total) -> vcm_status {
+            total = 0.0;
+            for (const Canon *c : mine) {
+                std::vector<const Canon *> one{c};
+                std::vector<vcm_tune> sh{t};
+                float *vv[1] = {d_v};
+                vcm_status st2 = enqueue_launch(ctx, ctx->direct, one, sh, vv, nullptr, nullptr, d_stats, s);
+                if (st2 != VCM_OK)
+                    return st2;
+                float best_one = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    CUDA_TRY(cudaEventRecord(e0, s));
+                    if ((st2 = enqueue_launch(ctx, ctx->direct, one, sh, vv, nullptr, nullptr, d_stats, s)) != VCM_OK)
+                        return st2;
+                    CUDA_TRY(cudaEventRecord(e1, s));
+                    CUDA_TRY(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                    best_one = std::min(best_one, ms);
+                }
+                total += best_one;
+            }
+            return VCM_OK;
+        };
         for (int cls = 0; cls < kTuneClasses; ++cls) {
             std::vector<const Canon *> mine;
             for (auto &c : cs)
@@ -1785,29 +1807,18 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
             if (mine.empty())
                 continue;
             seen[cls] = true;
+            // start from the default and move only on a clear (3 %) gain
+            best[cls] = default_tune();
+            if ((st = time_shape(mine, best[cls], best_ms[cls])) != VCM_OK)
+                return st;
             for (auto &tl : tiles)
                 for (uint32_t cap : caps)
                     for (uint32_t k : ks) {
                         vcm_tune t{tl[0], tl[1], k, cap};
                         double total = 0.0;
-                        for (const Canon *c : mine) {
-                            std::vector<const Canon *> one{c};
-                            std::vector<vcm_tune> sh{t};
-                            float *vv[1] = {d_v};
-                            // one warm launch, one timed launch
-                            for (int rep = 0; rep < 2; ++rep) {
-                                if (rep == 1)
-                                    CUDA_TRY(cudaEventRecord(e0, s));
-                                if ((st = enqueue_launch(ctx, ctx->direct, one, sh, vv, nullptr, nullptr, d_stats, s)) != VCM_OK)
-                                    return st;
-                            }
-                            CUDA_TRY(cudaEventRecord(e1, s));
-                            CUDA_TRY(cudaEventSynchronize(e1));
-                            float ms = 0.f;
-                            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-                            total += ms;
-                        }
-                        if (total < best_ms[cls]) {
+                        if ((st = time_shape(mine, t, total)) != VCM_OK)
+                            return st;
+                        if (total < 0.97 * best_ms[cls]) {
                             best_ms[cls] = total;
                             best[cls] = t;
                         }

@@ -434,3 +434,62 @@ def test_viewer_mode(ctx, which):
         assert (gv == 0).all() and gb.all()
     else:
         assert (gv > 0).sum() > 200 and gb.any()
+
+
+# ---------------------------------------------------------------------------
+# tuning, scene files and profiling hooks through the C ABI
+# ---------------------------------------------------------------------------
+
+def test_autotune_keeps_results(ctx):
+    sc, reqs = synth.workload_batched(seed=15, n_requests=4, n_boxes=3000, min_side=3, max_side=5)
+    load(ctx, sc, 50.0)
+    before = [_bits_and_v(ctx, dict(r, flags=1)) for r in reqs]
+    shapes = ctx.vcm_autotune(reqs)
+    assert len(shapes) == len(reqs) and all(s[0] >= 1 and s[3] >= 32 for s in shapes)
+    assert ctx.vcm_get_tune(reqs[0])[:2] == shapes[0][:2]
+    after = [_bits_and_v(ctx, dict(r, flags=1)) for r in reqs]
+    for a, b in zip(before, after):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_scene_file_round_trip_and_bad_files(ctx, tmp_path):
+    from paper_1310_7297_gb300 import VcmError
+
+    sc, req = synth.workload_2d(seed=16)
+    load(ctx, sc)
+    ref = _bits_and_v(ctx, req)
+    path = str(tmp_path / "scene.vcms")
+    ctx.vcm_scene_save(path)
+    ctx.vcm_scene_load(path)
+    ctx.vcm_build(0.0)
+    got = _bits_and_v(ctx, req)
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    raw = open(path, "rb").read()
+    for bad in (b"", b"VCMX" + raw[4:], raw[:-3], raw + b"\0"):
+        p = tmp_path / "bad.vcms"
+        p.write_bytes(bad)
+        with pytest.raises(VcmError) as e:
+            ctx.vcm_scene_load(str(p))
+        assert e.value.status == -2    # VCM_E_IO
+    with pytest.raises(VcmError) as e:
+        ctx.vcm_scene_load(str(tmp_path / "missing.vcms"))
+    assert e.value.status == -2
+
+
+def test_timing_events_bracket_the_tile_kernel(ctx):
+    import torch
+
+    sc, req = synth.workload_2d(seed=17)
+    load(ctx, sc)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    b.record()
+    ctx.vcm_set_timing_events(a, b)
+    try:
+        ctx.compute(req)
+        torch.cuda.synchronize()
+        assert a.elapsed_time(b) > 0.0
+    finally:
+        ctx.vcm_set_timing_events(None, None)
