@@ -313,6 +313,12 @@ void fill_shape(const Canon &c, const vcm_tune &t, DevRequest &d)
     d.n_tiles = d.tiles_x * d.tiles_y * c.nl;
 }
 
+// Scheduler thresholds, in viewpoint-patch segments: batches up to
+// kSmallWork run on high-priority slots; a batch stops growing past
+// kBatchWork (a request larger than that runs alone).
+constexpr double kSmallWork = 2.0e8;
+constexpr double kBatchWork = 1.0e9;
+
 int tune_class(int P)
 {
     if (P <= 32)
@@ -389,6 +395,9 @@ struct Slot {
     int *d_work = nullptr;
     int *d_spill = nullptr;
     size_t spill_cap = 0;   // ints
+    int *d_spill_busy = nullptr;   // spill-region claims of one-tile launches
+    size_t spill_busy_cap = 0;
+    bool high_priority = false;
     vcm_stats *d_stats = nullptr;
     size_t stats_cap = 0;   // entries
     bool busy = false;
@@ -579,7 +588,7 @@ vcm_status ensure_slot(vcm_ctx *ctx, Slot &s, size_t desc_bytes, size_t n_stats,
 {
     const size_t spill_need = (size_t)grid_blocks * std::max<uint32_t>(ctx->n_boxes, 1);
     const bool grow = desc_bytes > s.desc_cap || spill_need > s.spill_cap || n_stats > s.stats_cap ||
-                      !s.d_work;
+                      !s.d_work || (size_t)grid_blocks > s.spill_busy_cap;
     if (!grow)
         return VCM_OK;
     // the slot's buffers may still be read by queued work
@@ -613,6 +622,14 @@ vcm_status ensure_slot(vcm_ctx *ctx, Slot &s, size_t desc_bytes, size_t n_stats,
         s.d_spill = nullptr;
         CUDA_TRY(cudaMalloc(&s.d_spill, spill_need * sizeof(int)));
         s.spill_cap = spill_need;
+    }
+    if ((size_t)grid_blocks > s.spill_busy_cap) {
+        if (s.d_spill_busy) cudaFree(s.d_spill_busy);
+        s.d_spill_busy = nullptr;
+        CUDA_TRY(cudaMalloc(&s.d_spill_busy, (size_t)grid_blocks * sizeof(int)));
+        // on the launch stream: the slots' streams do not wait for the legacy default stream
+        CUDA_TRY(cudaMemsetAsync(s.d_spill_busy, 0, (size_t)grid_blocks * sizeof(int), sync_stream));
+        s.spill_busy_cap = (size_t)grid_blocks;
     }
     if (n_stats > s.stats_cap) {
         size_t cap = std::max<size_t>(n_stats, 256);
@@ -670,7 +687,7 @@ vcm_status prepare_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *
 // kernel and the quantiser, in stream order.  The node sequence is the same
 // for every launch, so a captured graph can be updated in place.
 vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *stats, cudaStream_t stream,
-                         bool timed = false, bool capturing = false)
+                         bool timed = false, bool capturing = false, bool one_tile = false)
 {
     CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, P.L.bytes, cudaMemcpyHostToDevice, stream));
     // An event recorded inside a stream capture cannot be waited on later;
@@ -686,7 +703,7 @@ vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *st
     if (timed && ctx->ev_before)
         CUDA_TRY(cudaEventRecord(ctx->ev_before, stream));
     CUDA_TRY(launch_tiles(ctx->scene, d_reqs, d_tiles, (int)P.n, P.L.total_tiles, s.d_work, s.d_spill,
-                          P.blocks, P.box_cap, 16, stream));
+                          P.blocks, P.box_cap, 16, stream, one_tile, s.d_spill_busy));
     if (timed && ctx->ev_after)
         CUDA_TRY(cudaEventRecord(ctx->ev_after, stream));
     CUDA_TRY(launch_quantise(d_reqs, d_vps, (int)P.n, P.L.total_vp, stream));
@@ -708,14 +725,15 @@ vcm_status enqueue_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *
 // the topology allows, re-instantiated otherwise) and launched.
 vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *> &cs,
                          const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
-                         uint32_t *const *bits, vcm_stats *stats)
+                         uint32_t *const *bits, vcm_stats *stats, bool one_tile)
 {
     Prepared P;
     vcm_status st = prepare_launch(ctx, s, cs, shapes, v, color, bits, stats, s.stream, P);
     if (st != VCM_OK)
         return st;
     CUDA_TRY(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeRelaxed));
-    st = record_launch(ctx, s, P, stats, s.stream, false, true);
+    // one_tile: one block per tile, so launches of other slots interleave
+    st = record_launch(ctx, s, P, stats, s.stream, false, true, one_tile);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s.stream, &g);
     if (st != VCM_OK) {
@@ -889,8 +907,10 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
         bits.push_back(t->d_bits);
     }
     vcm_status st = ensure_slot(ctx, s, 0, group.size(), 1, s.stream);
+    // one block per tile even when alone: a persistent grid would shut out
+    // requests that arrive while it runs
     if (st == VCM_OK)
-        st = enqueue_graph(ctx, s, cs, shapes, v.data(), col.data(), bits.data(), s.d_stats);
+        st = enqueue_graph(ctx, s, cs, shapes, v.data(), col.data(), bits.data(), s.d_stats, true);
     if (st == VCM_OK) {
         for (size_t i = 0; i < group.size(); ++i) {
             Ticket &t = *group[i];
@@ -924,81 +944,115 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
     }
 }
 
+enum SchedStep { STEP_WAIT, STEP_LAUNCHED, STEP_PROGRESS };
+
+// One scheduling decision (ctx->mu held): admit a batch from the head of the
+// queue onto a free slot and launch it.  Called by the scheduler thread and,
+// once, inline by vcm_submit so that a request that can start at once does
+// not wait for a thread hand-off.
+SchedStep schedule_once(vcm_ctx *ctx)
+{
+    // Small work goes to a free high-priority slot (its blocks start as
+    // soon as blocks of a running big launch finish); big work to a
+    // low-priority one.  Either may use the other kind when that is all
+    // that is free.
+    double head_work = 0.0;
+    if (!ctx->queue.empty())
+        for (auto &t : ctx->queue.front())
+            head_work += (double)t->canon.n_vp * t->canon.P;
+    const bool small = head_work <= kSmallWork;
+    Slot *free_slot = nullptr;
+    for (int pass = 0; pass < 2 && !free_slot; ++pass)
+        for (auto &s : ctx->slots)
+            if (!s->busy && (pass == 1 || s->high_priority == small)) {
+                free_slot = s.get();
+                break;
+            }
+    if (ctx->queue.empty() || !free_slot)
+        return STEP_WAIT;
+    // admit groups from the front of the queue while memory allows
+    std::vector<std::shared_ptr<Ticket>> batch;
+    bool alloc_failed = false;
+    double batch_work = 0.0;
+    while (!ctx->queue.empty()) {
+        auto &grp = ctx->queue.front();
+        size_t need = 0;
+        double work = 0.0;
+        for (auto &t : grp) {
+            need += t->canon.out_bytes() + 1024;
+            work += (double)t->canon.n_vp * t->canon.P;
+        }
+        if (!batch.empty() && batch.size() + grp.size() > ctx->max_batch)
+            break;
+        // a batch completes as a whole: keep small requests out of big batches
+        if (!batch.empty() && batch_work + work > kBatchWork)
+            break;
+        if (ctx->used + need > ctx->budget)
+            break;
+        bool ok = true;
+        for (auto &t : grp) {
+            if (!alloc_buffers(ctx, *t, free_slot->stream)) {
+                ok = false;
+                break;
+            }
+            t->bytes = t->canon.out_bytes() + 1024;
+            ctx->used += t->bytes;
+        }
+        if (!ok) {
+            for (auto &t : grp)
+                release_buffers(ctx, *t);
+            alloc_failed = true;
+            break;
+        }
+        for (auto &t : grp)
+            batch.push_back(t);
+        batch_work += work;
+        ctx->queue.pop_front();
+    }
+    if (batch.empty()) {
+        // The head does not fit the budget: finished results still hold
+        // memory until released, so wait.  Only a device allocation that
+        // fails with nothing in flight is final.
+        if (alloc_failed && ctx->running_groups == 0) {
+            auto grp = ctx->queue.front();
+            ctx->queue.pop_front();
+            for (auto &t : grp) {
+                t->state = T_ERROR;
+                t->err = VCM_E_NOMEM;
+                t->msg = "request does not fit in device memory";
+                t->t_done = std::chrono::steady_clock::now();
+            }
+            return STEP_PROGRESS;
+        }
+        return STEP_WAIT;
+    }
+    launch_group(ctx, *free_slot, batch);
+    return STEP_LAUNCHED;
+}
+
 void scheduler_loop(vcm_ctx *ctx)
 {
     cudaSetDevice(ctx->device);
     std::unique_lock<std::mutex> lk(ctx->mu);
     while (!ctx->stop) {
-        Slot *free_slot = nullptr;
-        for (auto &s : ctx->slots)
-            if (!s->busy) {
-                free_slot = s.get();
-                break;
-            }
-        if (ctx->queue.empty() || !free_slot) {
+        const SchedStep st = schedule_once(ctx);
+        if (st == STEP_WAIT)
             ctx->cv.wait(lk);
-            continue;
-        }
-        // admit groups from the front of the queue while memory allows
-        std::vector<std::shared_ptr<Ticket>> batch;
-        bool alloc_failed = false;
-        while (!ctx->queue.empty()) {
-            auto &grp = ctx->queue.front();
-            size_t need = 0;
-            for (auto &t : grp)
-                need += t->canon.out_bytes() + 1024;
-            if (!batch.empty() && batch.size() + grp.size() > ctx->max_batch)
-                break;
-            if (ctx->used + need > ctx->budget)
-                break;
-            bool ok = true;
-            for (auto &t : grp) {
-                if (!alloc_buffers(ctx, *t, free_slot->stream)) {
-                    ok = false;
-                    break;
-                }
-                t->bytes = t->canon.out_bytes() + 1024;
-                ctx->used += t->bytes;
-            }
-            if (!ok) {
-                for (auto &t : grp)
-                    release_buffers(ctx, *t);
-                alloc_failed = true;
-                break;
-            }
-            for (auto &t : grp)
-                batch.push_back(t);
-            ctx->queue.pop_front();
-        }
-        if (batch.empty()) {
-            // The head does not fit the budget: finished results still hold
-            // memory until released, so wait.  Only a device allocation that
-            // fails with nothing in flight is final.
-            if (alloc_failed && ctx->running_groups == 0) {
-                auto grp = ctx->queue.front();
-                ctx->queue.pop_front();
-                for (auto &t : grp) {
-                    t->state = T_ERROR;
-                    t->err = VCM_E_NOMEM;
-                    t->msg = "request does not fit in device memory";
-                    t->t_done = std::chrono::steady_clock::now();
-                }
-                ctx->cv.notify_all();
-            } else {
-                ctx->cv.wait(lk);
-            }
-            continue;
-        }
-        launch_group(ctx, *free_slot, batch);
-        ctx->cv.notify_all();
+        else
+            ctx->cv.notify_all();
     }
 }
 
 vcm_status start_scheduler(vcm_ctx *ctx, uint32_t n_slots)
 {
+    int prio_low = 0, prio_high = 0;
+    CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
     for (uint32_t i = 0; i < n_slots; ++i) {
         auto s = std::make_unique<Slot>();
-        CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+        // the first half of the slots run small batches at high priority
+        s->high_priority = n_slots > 1 && i < n_slots / 2;
+        CUDA_TRY(cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking,
+                                              s->high_priority ? prio_high : prio_low));
         CUDA_TRY(cudaEventCreateWithFlags(&s->desc_copied, cudaEventDisableTiming));
         CUDA_TRY(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
         ctx->slots.push_back(std::move(s));
@@ -1035,6 +1089,7 @@ void destroy_slot(Slot &s)
     if (s.h_desc) cudaFreeHost(s.h_desc);
     if (s.d_work) cudaFree(s.d_work);
     if (s.d_spill) cudaFree(s.d_spill);
+    if (s.d_spill_busy) cudaFree(s.d_spill_busy);
     if (s.d_stats) cudaFree(s.d_stats);
     if (s.desc_copied) cudaEventDestroy(s.desc_copied);
     if (s.done) cudaEventDestroy(s.done);
@@ -1044,8 +1099,8 @@ void destroy_slot(Slot &s)
     s.desc_copied = s.done = nullptr;
     s.d_desc = s.h_desc = nullptr;
     s.desc_cap = 0;
-    s.d_work = s.d_spill = nullptr;
-    s.spill_cap = 0;
+    s.d_work = s.d_spill = s.d_spill_busy = nullptr;
+    s.spill_cap = s.spill_busy_cap = 0;
     s.d_stats = nullptr;
     s.stats_cap = 0;
     s.busy = s.posted = false;
@@ -1419,6 +1474,7 @@ vcm_status vcm_submit_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, u
             tickets[i] = t->id;
         }
         ctx->queue.push_back(grp);
+        (void)schedule_once(ctx);   // start at once when a slot is free
         ctx->cv.notify_all();
         return VCM_OK;
     } catch (const std::exception &ex) {

@@ -17,6 +17,7 @@ constexpr float kBand = 1e-6f;            // FP32 slab margin re-decided in FP64
 constexpr int kMaxBoxCap = 5000;          // candidate boxes a tile stages in shared memory
 constexpr int kPyramidMinCount = 64;      // candidate lists longer than this get the pyramid filter
 constexpr int kMaxTileViewpoints = 1024;  // viewpoints in one tile (tile_x * tile_y)
+constexpr int kClaimRounds = 4096;        // bounded retries of a spill-region claim (2 us pauses)
 
 inline size_t tiles_smem_bytes(int box_cap) { return (size_t)box_cap * (32 + 4); }
 
@@ -74,13 +75,18 @@ cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, 
                               int *d_cell_start, float4 *const *d_perm_boxes, float4 *d_cell_lo,
                               float4 *d_cell_hi, unsigned *d_overhang_bits, cudaStream_t stream);
 
-// The persistent tile kernel over `n_req` requests (their tiles concatenated,
-// `d_tile_prefix` = exclusive prefix of tiles, n_req + 1 entries).  The
-// kernel draws tiles from `d_work` (zeroed by the caller).  `d_spill` holds
+// The tile kernel over `n_req` requests (their tiles concatenated,
+// `d_tile_prefix` = exclusive prefix of tiles, n_req + 1 entries).  Persistent
+// by default: grid_blocks blocks draw tiles from `d_work` (zeroed by the
+// caller).  With one_tile, one block per tile, so concurrent launches
+// interleave block by block; grid_blocks must then be at least the number of
+// blocks that can be resident at once, and `d_spill_busy` (grid_blocks ints,
+// all zero between launches) hands out the spill regions.  `d_spill` holds
 // grid_blocks * n_boxes ints for candidate lists longer than box_cap.
 cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
                          int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
-                         int box_cap, int k_rows_max, cudaStream_t stream);
+                         int box_cap, int k_rows_max, cudaStream_t stream, bool one_tile = false,
+                         int *d_spill_busy = nullptr);
 
 // Colors and edge counts for all viewpoints of n_req requests (grid over the
 // concatenated viewpoints, `d_vp_prefix` = exclusive prefix, n_req + 1).

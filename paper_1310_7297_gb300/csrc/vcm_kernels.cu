@@ -698,7 +698,8 @@ __device__ __forceinline__ float sweep_k(const DevRequest &R, const float4 *sbox
 
 __global__ void __launch_bounds__(kThreads, 4)
 k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict__ tile_prefix,
-        int n_req, int total_tiles, int *__restrict__ work, int *__restrict__ spill_all, int box_cap)
+        int n_req, int total_tiles, int *__restrict__ work, int *__restrict__ spill_all, int box_cap,
+        int one_tile, int *__restrict__ spill_busy, int spill_slots)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *s_box = reinterpret_cast<float4 *>(smem_raw);
@@ -711,15 +712,43 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
     __shared__ int s_req_idx;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    int *spill = spill_all + (size_t)blockIdx.x * sc.n_boxes;
-    if (tid == 0)
+    __shared__ int s_spill_slot;
+    if (tid == 0) {
         s_req_idx = -1;
+        sm.item = -1;
+        // A persistent block owns spill region blockIdx.x.  A one-tile block
+        // claims a free region for the length of its tile.  There are as
+        // many regions as blocks fit on the GPU, so a probe normally succeeds
+        // at once; if every region is held (blocks of a preempted launch keep
+        // theirs), it probes again after a pause, at most kClaimRounds times
+        // (a few ms), and then runs without one and flags the result.
+        int slot = (int)blockIdx.x;
+        if (one_tile) {
+            slot = -1;
+            const int start = (int)(blockIdx.x % (unsigned)spill_slots);
+            for (int round = 0; round < kClaimRounds && slot < 0; ++round) {
+                for (int probe = 0; probe < spill_slots && slot < 0; ++probe) {
+                    const int c = (start + probe) % spill_slots;
+                    if (atomicCAS(&spill_busy[c], 0, 1) == 0)
+                        slot = c;
+                }
+                if (slot < 0)
+                    __nanosleep(2000);
+            }
+        }
+        s_spill_slot = slot;
+    }
+    __syncthreads();
+    const int spill_slot = s_spill_slot;
+    int *spill = spill_all + (size_t)max(spill_slot, 0) * sc.n_boxes;
 
     for (;;) {
         // thread 0 takes the next tile, copies its request and lays out the
-        // hull points (one barrier for all of it)
+        // hull points (one barrier for all of it).  With one_tile, block b
+        // does tile b only and exits, so blocks of concurrent launches
+        // interleave (a persistent grid would hold every SM to the end).
         if (tid == 0) {
-            const int it = atomicAdd(work, 1);
+            const int it = one_tile ? (sm.item == -2 ? total_tiles : (int)blockIdx.x) : atomicAdd(work, 1);
             sm.item = it;
             if (it < total_tiles) {
                 // request of this tile: last r with tile_prefix[r] <= it
@@ -803,6 +832,8 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 R.v_out[((long long)layer * R.ny + iy) * R.nx + ix] = 0.f;
             }
             __syncthreads();
+            if (tid == 0)
+                sm.item = -2;
             continue;
         }
 
@@ -839,8 +870,10 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                     const int pos = atomicAdd(&sm.count, 1);
                     if (pos < box_cap)
                         s_ids[pos] = s;
-                    else
+                    else if (spill_slot >= 0)
                         spill[pos - box_cap] = s;
+                    else
+                        R.stats->error = 2u;   // no spill region: the result is flagged
                 }
             }
         }
@@ -996,10 +1029,14 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             rechecks += __shfl_xor_sync(kFull, rechecks, off);
         if (lane == 0 && rechecks)
             atomicAdd(&R.stats->rechecked, (unsigned long long)rechecks);
-        if (tid == 0)
+        if (tid == 0) {
             atomicAdd(&R.stats->boxes_listed, (unsigned long long)count);
+            sm.item = -2;   // one_tile: the next round exits
+        }
         __syncthreads();
     }
+    if (one_tile && tid == 0 && spill_slot >= 0)
+        atomicExch(&spill_busy[spill_slot], 0);
 }
 
 // Clear the occlusion-bit buffers of the requests that asked for bits
@@ -1163,7 +1200,7 @@ int tiles_blocks_per_sm(int box_cap, int k_rows_max)
 
 cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
                          int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
-                         int box_cap, int k_rows_max, cudaStream_t stream)
+                         int box_cap, int k_rows_max, cudaStream_t stream, bool one_tile, int *d_spill_busy)
 {
     (void)k_rows_max;
     if (total_tiles <= 0)
@@ -1171,8 +1208,15 @@ cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int
     if (box_cap < 1 || box_cap > kMaxBoxCap)
         return cudaErrorInvalidValue;
     const size_t smem = tiles_smem_bytes(box_cap);
+    const int slots = grid_blocks;   // spill regions: the resident-block bound
+    if (one_tile) {
+        if (!d_spill_busy)
+            return cudaErrorInvalidValue;
+        grid_blocks = total_tiles;
+    }
     k_tiles<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles,
-                                                     d_work, d_spill, box_cap);
+                                                     d_work, d_spill, box_cap, one_tile ? 1 : 0,
+                                                     d_spill_busy, slots);
     return cudaGetLastError();
 }
 

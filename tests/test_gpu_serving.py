@@ -94,3 +94,25 @@ def test_cancel_queued_request(scene_reqs):
         ctx.vcm_result_release(tickets[-1])
     finally:
         ctx.close()
+
+
+def test_scheduler_spill_path_matches_direct(scene_reqs):
+    """Scheduler launches run one block per tile and claim spill regions from a
+    per-slot pool; with 32 staged boxes most candidate lists spill."""
+    scene, reqs = scene_reqs
+    ctx = _ctx(scene)
+    try:
+        ctx.vcm_set_tune(16, 8, 8, 32)
+        alone = [gpu_run(ctx, dict(r, flags=1), bits=True) for r in reqs[:6]]
+        for rep in range(2):
+            tickets = [ctx.vcm_submit(dict(r, flags=1)) for r in reqs[:6]]
+            for i, t in enumerate(tickets):
+                assert ctx.vcm_poll(t, -1) == 0
+                v, c, b, st = ctx.vcm_result_get(t)
+                assert st["error"] == 0 and st["boxes_listed"] > 0
+                assert np.array_equal(v.astype(np.float64), alone[i][0])
+                assert np.array_equal(b, alone[i][2])
+                ctx.vcm_result_release(t)
+    finally:
+        ctx.vcm_set_tune(0)
+        ctx.close()
