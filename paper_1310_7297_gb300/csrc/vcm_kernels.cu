@@ -246,6 +246,7 @@ struct TileSmem {
     int count;
     int item;
     int pad;
+    int n_und;
 };
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
@@ -345,6 +346,30 @@ __device__ void hull_planes(int dims, const float (*P)[3], int np, TileSmem &sm)
         if (slot < kMaxPlanes)
             sm.planes[slot] = Plane{n3[0], n3[1], n3[2], c};
     }
+}
+
+// True if the box [lo, hi] (target frame) certainly (margin > band) blocks
+// the segments from q to all four extreme patch centres; see below.
+__device__ __forceinline__ bool box_blocks_all(const DevRequest &R, float4 lo, float4 hi, float qu, float qn,
+                                               float qw)
+{
+    const float du0 = R.u_min - qu, du1 = R.u_max - qu;
+    const float dn = R.p_n - qn;
+    const float dw0 = R.w_min - qw, dw1 = R.w_max - qw;
+    const float iu0 = rcp_approx(du0), iu1 = rcp_approx(du1), inn = rcp_approx(dn);
+    const float iw0 = rcp_approx(dw0), iw1 = rcp_approx(dw1);
+    const float au = lo.x - qu, bu = hi.x - qu, an = lo.y - qn, bn = hi.y - qn;
+    const float aw = lo.z - qw, bw = hi.z - qw;
+    const float nu0 = (du0 >= 0.f ? au : bu) * iu0, fu0 = (du0 >= 0.f ? bu : au) * iu0;
+    const float nu1 = (du1 >= 0.f ? au : bu) * iu1, fu1 = (du1 >= 0.f ? bu : au) * iu1;
+    const float nw0 = (dw0 >= 0.f ? aw : bw) * iw0, fw0 = (dw0 >= 0.f ? bw : aw) * iw0;
+    const float nw1 = (dw1 >= 0.f ? aw : bw) * iw1, fw1 = (dw1 >= 0.f ? bw : aw) * iw1;
+    const float e0 = fmaxf((dn >= 0.f ? an : bn) * inn, 0.f);
+    const float x0 = fminf((dn >= 0.f ? bn : an) * inn, 1.f);
+    return fminf(fminf(fu0, fw0), x0) - fmaxf(fmaxf(nu0, nw0), e0) > kBand &&
+           fminf(fminf(fu1, fw0), x0) - fmaxf(fmaxf(nu1, nw0), e0) > kBand &&
+           fminf(fminf(fu0, fw1), x0) - fmaxf(fmaxf(nu0, nw1), e0) > kBand &&
+           fminf(fminf(fu1, fw1), x0) - fmaxf(fmaxf(nu1, nw1), e0) > kBand;
 }
 
 // True if one of the first `nb` (<= 32) staged boxes certainly blocks the
@@ -710,6 +735,8 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
     __shared__ int s_next;
     __shared__ Plane s_pyr[kWarps][6];
     __shared__ int s_req_idx;
+    __shared__ int s_next2;                     // cursor of the undecided list
+    __shared__ int s_und[kMaxTileViewpoints];   // viewpoints left by the one-box check
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     __shared__ int s_spill_slot;
@@ -774,7 +801,9 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 const float z = Q.z_coord[ly];
                 sm.n_planes = 0;
                 sm.count = 0;
+                sm.n_und = 0;
                 s_next = 0;
+                s_next2 = 0;
                 const float X[2] = {Q.x_coord[x0], Q.x_coord[x1]};
                 const float Y[2] = {Q.y_coord[y0], Q.y_coord[y1]};
                 for (int c = 0; c < 4; ++c) {
@@ -963,57 +992,115 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 vmax = fmaxf(vmax, v);
             }
         }
+        // First every viewpoint gets the one-box check, four per warp with
+        // lanes as 4 viewpoints x the 8 nearest candidates (the blocking box
+        // is almost always among them); the viewpoints it leaves open are
+        // listed and then taken one per warp for the check over the 32
+        // nearest and the separable sweep.
         for (; !viewer;) {
-            int vi = 0;
+            int base = 0;
             if (lane == 0)
-                vi = atomicAdd(&s_next, 1);
-            vi = __shfl_sync(kFull, vi, 0);
-            if (vi >= tn)
+                base = atomicAdd(&s_next, 4);
+            base = __shfl_sync(kFull, base, 0);
+            if (base >= tn)
                 break;
-            const int ix = ix0 + vi % tw, iy = iy0 + vi / tw;
-            const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
-            const float qx = R.x_coord[ix], qy = R.y_coord[iy];
-            const float qu = R.au == 0 ? qx : (R.au == 1 ? qy : zq);
-            const float qn = R.an == 0 ? qx : (R.an == 1 ? qy : zq);
-            const float qw = R.dims == 3 ? (R.aw == 0 ? qx : (R.aw == 1 ? qy : zq)) : 0.f;
-            const bool front = R.sn * (qn - R.p_n) > 0.f;
-            if (!front && !want_bits) {
-                if (lane == 0)
-                    R.v_out[vp] = 0.f;
-                continue;
-            }
-            const int nb_short = min(n_smem, 32);
-            corner_tests += 4ull * nb_short;
-            if (n_smem > 0 && one_box_blocks_all(R, s_box, nb_short, qu, qn, qw)) {
-                ++shortcuts;
-                if (lane == 0)
-                    R.v_out[vp] = 0.f;
-                if (want_bits)
-                    for (int wd = lane; wd < R.words; wd += 32) {
-                        const int rem = R.P - 32 * wd;
-                        R.bits_out[vp * R.words + wd] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+            const int sub = lane >> 3, bl = lane & 7;
+            const int nb8 = min(n_smem, 8);
+            {
+                const int vi = base + sub;
+                long long vp = 0;
+                bool active = false, behind = false, full = false;
+                if (vi < tn) {
+                    const int ix = ix0 + vi % tw, iy = iy0 + vi / tw;
+                    vp = ((long long)layer * R.ny + iy) * R.nx + ix;
+                    const float qx = R.x_coord[ix], qy = R.y_coord[iy];
+                    const float qu = R.au == 0 ? qx : (R.au == 1 ? qy : zq);
+                    const float qn = R.an == 0 ? qx : (R.an == 1 ? qy : zq);
+                    const float qw = R.dims == 3 ? (R.aw == 0 ? qx : (R.aw == 1 ? qy : zq)) : 0.f;
+                    active = want_bits || R.sn * (qn - R.p_n) > 0.f;
+                    behind = !active;
+                    if (active && bl < nb8) {
+                        full = box_blocks_all(R, s_box[2 * bl], s_box[2 * bl + 1], qu, qn, qw);
+                        corner_tests += 4;
                     }
-                continue;
+                }
+                const unsigned m = __ballot_sync(kFull, full);
+                const bool decided = active && ((m >> (8 * sub)) & 0xffu) != 0;
+                if (behind && bl == 0)
+                    R.v_out[vp] = 0.f;   // behind the target
+                if (decided) {
+                    if (bl == 0) {
+                        R.v_out[vp] = 0.f;
+                        ++shortcuts;
+                    }
+                    if (want_bits)
+                        for (int wd = bl; wd < R.words; wd += 8) {
+                            const int rem = R.P - 32 * wd;
+                            R.bits_out[vp * R.words + wd] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+                        }
+                }
+                if (active && !decided && bl == 0)
+                    s_und[atomicAdd(&sm.n_und, 1)] = vi;
             }
-            // the pyramid filter pays for its set-up only on long candidate lists
-            Plane *pyr = s_pyr[warp];
-            const int npyr = count > kPyramidMinCount ? pyramid_planes(R, qu, qn, qw, pyr) : 0;
-            float v;
-            switch (R.k_rows) {
-            case 1: v = sweep_k<1>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
-            case 2: v = sweep_k<2>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
-            case 4: v = sweep_k<4>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
-            default: v = sweep_k<8>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
-            }
-            if (!front)
-                v = 0.f;
+        }
+        __syncthreads();
+        // then the undecided viewpoints, one per warp at a time
+        const int n_und = viewer ? 0 : sm.n_und;
+        for (;;) {
+            int k = 0;
             if (lane == 0)
-                R.v_out[vp] = v;
-            vmax = fmaxf(vmax, v);
+                k = atomicAdd(&s_next2, 1);
+            k = __shfl_sync(kFull, k, 0);
+            if (k >= n_und)
+                break;
+            {
+                const int vi = s_und[k];
+                const int ix = ix0 + vi % tw, iy = iy0 + vi / tw;
+                const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
+                const float qx = R.x_coord[ix], qy = R.y_coord[iy];
+                const float qu = R.au == 0 ? qx : (R.au == 1 ? qy : zq);
+                const float qn = R.an == 0 ? qx : (R.an == 1 ? qy : zq);
+                const float qw = R.dims == 3 ? (R.aw == 0 ? qx : (R.aw == 1 ? qy : zq)) : 0.f;
+                const bool front = R.sn * (qn - R.p_n) > 0.f;
+                if (n_smem > 8) {
+                    const int nb_short = min(n_smem, 32);
+                    if (lane < nb_short)
+                        corner_tests += 4;
+                    if (one_box_blocks_all(R, s_box, nb_short, qu, qn, qw)) {
+                        if (lane == 0) {
+                            R.v_out[vp] = 0.f;
+                            ++shortcuts;
+                        }
+                        if (want_bits)
+                            for (int wd = lane; wd < R.words; wd += 32) {
+                                const int rem = R.P - 32 * wd;
+                                R.bits_out[vp * R.words + wd] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+                            }
+                        continue;
+                    }
+                }
+                // the pyramid filter pays for its set-up only on long candidate lists
+                Plane *pyr = s_pyr[warp];
+                const int npyr = count > kPyramidMinCount ? pyramid_planes(R, qu, qn, qw, pyr) : 0;
+                float v;
+                switch (R.k_rows) {
+                case 1: v = sweep_k<1>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+                case 2: v = sweep_k<2>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+                case 4: v = sweep_k<4>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+                default: v = sweep_k<8>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+                }
+                if (!front)
+                    v = 0.f;
+                if (lane == 0)
+                    R.v_out[vp] = v;
+                vmax = fmaxf(vmax, v);
+            }
         }
         // per-tile counters
         for (int off = 16; off > 0; off >>= 1) {
             tests += __shfl_xor_sync(kFull, tests, off);
+            corner_tests += __shfl_xor_sync(kFull, corner_tests, off);
+            shortcuts += __shfl_xor_sync(kFull, shortcuts, off);
             vmax = fmaxf(vmax, __shfl_xor_sync(kFull, vmax, off));
         }
         if (lane == 0) {
