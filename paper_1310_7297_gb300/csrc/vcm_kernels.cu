@@ -737,6 +737,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
     __shared__ int s_req_idx;
     __shared__ int s_next2;                     // cursor of the undecided list
     __shared__ int s_und[kMaxTileViewpoints];   // viewpoints left by the one-box check
+    __shared__ int s_rowpre[kThreads], s_rowx[kThreads], s_wsum[kWarps];   // cell-row spans
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     __shared__ int s_spill_slot;
@@ -871,39 +872,110 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         __syncthreads();
         const int n_planes = min(sm.n_planes, kMaxPlanes);
 
-        // walk the grid cells under the hull's footprint
+        // walk the grid cells under the hull's footprint.  In the xy plane
+        // the footprint is the convex hull of two axis-aligned rectangles,
+        // A (the tile's viewpoints) and B (the target's shadow on the
+        // ground plane), which is the union over l in [0, 1] of the
+        // rectangles (1 - l) A + l B.  A row of cells meets it for the l whose
+        // rectangle reaches the row -- an interval, from two linear
+        // inequalities -- and over the x-range those rectangles sweep, which
+        // is spanned by the interval's two ends.  Rows are taken 128 at a
+        // time: one thread finds a row's span, a block scan lays the spans
+        // end to end, and the threads share out the cells.
         {
-            float bx0 = s_pts[0][0], bx1 = s_pts[0][0], by0 = s_pts[0][1], by1 = s_pts[0][1];
-            for (int l = 1; l < np; ++l) {
+            float ax0 = s_pts[0][0], ax1 = ax0, ay0 = s_pts[0][1], ay1 = ay0;
+            for (int l = 1; l < 4; ++l) {
+                ax0 = fminf(ax0, s_pts[l][0]); ax1 = fmaxf(ax1, s_pts[l][0]);
+                ay0 = fminf(ay0, s_pts[l][1]); ay1 = fmaxf(ay1, s_pts[l][1]);
+            }
+            float bx0 = s_pts[4][0], bx1 = bx0, by0 = s_pts[4][1], by1 = by0;
+            for (int l = 5; l < np; ++l) {
                 bx0 = fminf(bx0, s_pts[l][0]); bx1 = fmaxf(bx1, s_pts[l][0]);
                 by0 = fminf(by0, s_pts[l][1]); by1 = fmaxf(by1, s_pts[l][1]);
             }
-            const float oh = sc.overhang;
-            int cx0 = (int)floorf((bx0 - oh - sc.gx0) * sc.inv_cell) - 1;
-            int cx1 = (int)floorf((bx1 + oh - sc.gx0) * sc.inv_cell) + 1;
-            int cy0 = (int)floorf((by0 - oh - sc.gy0) * sc.inv_cell) - 1;
-            int cy1 = (int)floorf((by1 + oh - sc.gy0) * sc.inv_cell) + 1;
-            cx0 = max(cx0, 0); cy0 = max(cy0, 0);
-            cx1 = min(cx1, sc.gnx - 1); cy1 = min(cy1, sc.gny - 1);
-            const int wcx = cx1 - cx0 + 1;
-            const int ncell = (cx1 >= cx0 && cy1 >= cy0) ? wcx * (cy1 - cy0 + 1) : 0;
+            // how far a cell's boxes reach past the cell, plus 1 m: far more
+            // than the rounding of any quantity below (coordinates are
+            // within 2^14 m), so no cell that can hold an occluder is missed
+            const float oh = sc.overhang + 1.f;
+            const int cy0 = max((int)floorf((fminf(ay0, by0) - oh - sc.gy0) * sc.inv_cell), 0);
+            const int cy1 = min((int)floorf((fmaxf(ay1, by1) + oh - sc.gy0) * sc.inv_cell), sc.gny - 1);
+            const float dy0 = by0 - ay0, dy1 = by1 - ay1;
             const float4 *world = sc.boxes[0];
-            for (int c = tid; c < ncell; c += kThreads) {
-                const int cell = (cy0 + c / wcx) * sc.gnx + cx0 + c % wcx;
-                const int b = sc.cell_start[cell], e = sc.cell_start[cell + 1];
-                if (b == e || outside(sm.planes, n_planes, sc.cell_lo[cell], sc.cell_hi[cell]))
-                    continue;
-                for (int s = b; s < e; ++s) {
-                    if (outside(sm.planes, n_planes, world[2 * s], world[2 * s + 1]))
-                        continue;
-                    const int pos = atomicAdd(&sm.count, 1);
-                    if (pos < box_cap)
-                        s_ids[pos] = s;
-                    else if (spill_slot >= 0)
-                        spill[pos - box_cap] = s;
-                    else
-                        R.stats->error = 2u;   // no spill region: the result is flagged
+            for (int r0 = cy0; r0 <= cy1; r0 += kThreads) {
+                const int row = r0 + tid;
+                int xa = 0, width = 0;
+                if (row <= cy1) {
+                    const float ya = fmaf((float)row, sc.cell, sc.gy0) - oh, yb = ya + sc.cell + 2.f * oh;
+                    float l0 = 0.f, l1 = 1.f;
+                    // lower edge ay0 + l dy0 <= yb
+                    if (dy0 > 0.f)
+                        l1 = fminf(l1, (yb - ay0) / dy0);
+                    else if (dy0 < 0.f)
+                        l0 = fmaxf(l0, (yb - ay0) / dy0);
+                    else if (ay0 > yb)
+                        l1 = -1.f;
+                    // upper edge ay1 + l dy1 >= ya
+                    if (dy1 > 0.f)
+                        l0 = fmaxf(l0, (ya - ay1) / dy1);
+                    else if (dy1 < 0.f)
+                        l1 = fminf(l1, (ya - ay1) / dy1);
+                    else if (ay1 < ya)
+                        l1 = -1.f;
+                    if (l0 <= l1) {
+                        const float xl = fminf(fmaf(l0, bx0 - ax0, ax0), fmaf(l1, bx0 - ax0, ax0));
+                        const float xh = fmaxf(fmaf(l0, bx1 - ax1, ax1), fmaf(l1, bx1 - ax1, ax1));
+                        const int c0 = max((int)floorf((xl - oh - sc.gx0) * sc.inv_cell), 0);
+                        const int c1 = min((int)floorf((xh + oh - sc.gx0) * sc.inv_cell), sc.gnx - 1);
+                        if (c1 >= c0) {
+                            xa = c0;
+                            width = c1 - c0 + 1;
+                        }
+                    }
                 }
+                // exclusive scan of the widths over the block
+                int incl = width;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int t = __shfl_up_sync(kFull, incl, off);
+                    if (lane >= off)
+                        incl += t;
+                }
+                if (lane == 31)
+                    s_wsum[warp] = incl;
+                __syncthreads();
+                int before = 0, total = 0;
+#pragma unroll
+                for (int w2 = 0; w2 < kWarps; ++w2) {
+                    before += w2 < warp ? s_wsum[w2] : 0;
+                    total += s_wsum[w2];
+                }
+                s_rowpre[tid] = before + incl - width;
+                s_rowx[tid] = xa;
+                __syncthreads();
+                for (int c = tid; c < total; c += kThreads) {
+                    // the row of cell c: the last t with s_rowpre[t] <= c
+                    int t = 0;
+#pragma unroll
+                    for (int step = kThreads / 2; step > 0; step >>= 1)
+                        if (s_rowpre[t + step] <= c)
+                            t += step;
+                    const int cell = (r0 + t) * sc.gnx + s_rowx[t] + (c - s_rowpre[t]);
+                    const int b = sc.cell_start[cell], e = sc.cell_start[cell + 1];
+                    if (b == e || outside(sm.planes, n_planes, sc.cell_lo[cell], sc.cell_hi[cell]))
+                        continue;
+                    for (int s = b; s < e; ++s) {
+                        if (outside(sm.planes, n_planes, world[2 * s], world[2 * s + 1]))
+                            continue;
+                        const int pos = atomicAdd(&sm.count, 1);
+                        if (pos < box_cap)
+                            s_ids[pos] = s;
+                        else if (spill_slot >= 0)
+                            spill[pos - box_cap] = s;
+                        else
+                            R.stats->error = 2u;   // no spill region: the result is flagged
+                    }
+                }
+                __syncthreads();   // the next rows reuse the span arrays
             }
         }
         __syncthreads();

@@ -54,6 +54,22 @@ def test_workload_3d_reduced_full(ctx):
     assert (gv > 0).sum() > 500 and gb.any()
 
 
+@pytest.mark.parametrize("cell", [3.0, 1000.0])
+def test_grid_cell_sizes_walk_every_occluder(ctx, cell):
+    """The tile kernel walks only the cell rows under the hull's footprint.
+    A 3 m grid gives ~270 rows (several 128-row rounds and long diagonal
+    spans); a 1 km grid puts the scene in one or two cells.  Results must not
+    depend on it."""
+    sc, req = synth.workload_3d(seed=7, grid=40, layers=5, patches=(32, 16), n_boxes=800, half_m=400.0,
+                                n_components=6, sigma_m=(30.0, 120.0))
+    load(ctx, sc, cell)
+    gv, gb, st, err, mism = full_parity(ctx, sc, req)
+    assert (gv > 0).sum() > 500 and gb.any()
+    sc2, req2 = synth.workload_2d()
+    load(ctx, sc2, cell)
+    full_parity(ctx, sc2, req2)
+
+
 def test_workload_3d_full_size_sampled(ctx):
     """512 x 512 x 5 viewpoints, 5,000 boxes, 32 x 16 patches, in the launch
     configuration the benchmark times; the oracle checks 1,200 viewpoints."""
