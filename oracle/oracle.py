@@ -33,10 +33,11 @@ class VoRequest(ctypes.Structure):
                 ("patches_u", ctypes.c_int32), ("patches_w", ctypes.c_int32),
                 ("grid_origin", ctypes.c_int64 * 2), ("grid_step", ctypes.c_int64 * 2),
                 ("grid_nx", ctypes.c_int32), ("grid_ny", ctypes.c_int32),
-                ("n_layers", ctypes.c_int32), ("layer_z", _i64p), ("mode", ctypes.c_int32)]
+                ("n_layers", ctypes.c_int32), ("layer_z", _i64p), ("mode", ctypes.c_int32),
+                ("two_sided", ctypes.c_int32), ("fov_deg", ctypes.c_float), ("gaze", ctypes.c_float * 3)]
 
 MODE_PARTIAL, MODE_STRICT, MODE_VIEWER = 0, 1, 2
-FLAG_STRICT, FLAG_VIEWER = 2, 4   # request flag bits that select the modes
+FLAG_STRICT, FLAG_VIEWER, FLAG_TWO_SIDED = 2, 4, 8   # request flag bits that select the modes
 
 
 def build(force=False):
@@ -106,6 +107,11 @@ class _Pack:
         r.layer_z = _p64(self.req_layers)
         fl = int(req.get("flags", 0))
         r.mode = MODE_VIEWER if fl & FLAG_VIEWER else (MODE_STRICT if fl & FLAG_STRICT else MODE_PARTIAL)
+        r.two_sided = 1 if fl & FLAG_TWO_SIDED else 0
+        r.fov_deg = float(req.get("fov_deg", 0.0))
+        g = req.get("gaze", (0.0, 0.0, 0.0))
+        for k in range(3):
+            r.gaze[k] = float(g[k])
         self.s = None
         if scene is not None:
             self.lo = np.ascontiguousarray(scene.lo, dtype=np.int64)

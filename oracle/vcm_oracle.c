@@ -14,6 +14,7 @@
 #include <string.h>
 
 #define UNITS_PER_M 1024.0
+#define VO_PI 3.14159265358979323846
 #define COORD_LIMIT ((int64_t)1 << 24)
 
 static int axis_index(int32_t code) { return code >> 1; }
@@ -60,6 +61,11 @@ int vo_check(const vo_scene *s, const vo_request *r)
     }
     if (r->axis_u < 0 || r->axis_u > 5 || r->normal < 0 || r->normal > 5)
         return -1;
+    if ((r->two_sided != 0 && r->two_sided != 1) || !isfinite(r->fov_deg) || r->fov_deg < 0.0f)
+        return -1;
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(r->gaze[k]))
+            return -1;
     if (r->dims == 3) {
         if (r->axis_w < 0 || r->axis_w > 5)
             return -1;
@@ -196,6 +202,38 @@ static double viewer_value(const vo_scene *s, const vo_request *r, const int64_t
     return 4.0 * asin(S * S / (S * S + 4.0 * D * D));  /* S x S square facing the viewer */
 }
 
+/* Field of view (vcm_oracle.h): the cone's cosine c and unit axis a, or 0
+ * when there is no cone. */
+static int fov_setup(const vo_request *r, float *c, float a[3])
+{
+    if (!(r->fov_deg > 0.0f) || r->fov_deg >= 360.0f)
+        return 0;
+    *c = (float)cos((double)r->fov_deg * VO_PI / 360.0);
+    double g[3] = {r->gaze[0], r->gaze[1], r->dims == 3 ? r->gaze[2] : 0.0f};
+    if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0)
+        g[axis_index(r->normal)] = (double)axis_sign(r->normal);
+    double len = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    for (int k = 0; k < 3; ++k)
+        a[k] = (float)(g[k] / len);
+    return 1;
+}
+
+/* Is q inside the cone of patch p?  float32, one rounding per operation
+ * (the file is compiled without contraction into fused multiply-adds). */
+static int in_fov(const int64_t q[3], const int64_t p[3], float c, const float a[3], int two_sided)
+{
+    float rk[3];
+    for (int k = 0; k < 3; ++k)
+        rk[k] = (float)q[k] / 1024.0f - (float)p[k] / 1024.0f;   /* both exact; one rounding */
+    float d = a[0] * rk[0] + a[1] * rk[1];
+    d = d + a[2] * rk[2];
+    if (two_sided)
+        d = fabsf(d);
+    float rr = rk[0] * rk[0] + rk[1] * rk[1];
+    rr = rr + rk[2] * rk[2];
+    return d >= c * sqrtf(rr);
+}
+
 double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint32_t *bits)
 {
     int64_t q[3];
@@ -215,12 +253,17 @@ double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint
     int an = axis_index(r->normal);
     double sn = (double)axis_sign(r->normal);
     double measure = vo_patch_measure(r);
+    float fov_c = 0.0f, fov_a[3] = {0.0f, 0.0f, 0.0f};
+    int cone = fov_setup(r, &fov_c, fov_a);
     double sum = 0.0, comp = 0.0;   /* Neumaier running sum and compensation */
     int any_blocked = 0;
     for (int64_t j = 0; j < P; ++j) {
         const int64_t *p = pc + 3 * j;
-        /* cos(theta) * |r| = n . (q - p): positive in front of the target */
+        /* cos(theta) * |r| = n . (q - p): positive in front of the target;
+         * a two-sided target is seen from either side */
         double cos_r = sn * (double)(q[an] - p[an]) / UNITS_PER_M;
+        if (r->two_sided)
+            cos_r = fabs(cos_r);
         int blocked = 0;
         if (bits || cos_r > 0.0 || r->mode == VO_STRICT)
             blocked = patch_blocked(s, q, p);
@@ -229,6 +272,8 @@ double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint
             bits[j >> 5] |= 1u << (j & 31);
         if (blocked || !(cos_r > 0.0))
             continue;
+        if (cone && !in_fov(q, p, fov_c, fov_a, r->two_sided))
+            continue;   /* outside the target's field of view */
         double rx = (double)(q[0] - p[0]) / UNITS_PER_M;
         double ry = (double)(q[1] - p[1]) / UNITS_PER_M;
         double rz = (double)(q[2] - p[2]) / UNITS_PER_M;

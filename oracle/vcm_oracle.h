@@ -53,6 +53,9 @@ typedef struct {
     int32_t n_layers;
     const int64_t *layer_z;           /* [n_layers]; ignored in 2D */
     int32_t mode;                     /* VO_PARTIAL, VO_STRICT or VO_VIEWER */
+    int32_t two_sided;                /* 1: the target counts from both faces */
+    float fov_deg;                    /* field of view of the target; 0 or >= 360: none */
+    float gaze[3];                    /* axis of the field of view (world); 0,0,0: the normal */
 } vo_request;
 
 /* Modes.
@@ -69,6 +72,27 @@ typedef struct {
  *             viewer, and 0 if the segment to the viewer is blocked or D = 0.
  *             One occlusion bit per cell. */
 enum { VO_PARTIAL = 0, VO_STRICT = 1, VO_VIEWER = 2 };
+
+/* Sides and field of view (target-centric modes only).
+ * two_sided = 0: a patch counts only from the side its normal faces,
+ *   s = n.(q - p) > 0 (one-sided target; nothing counts from behind).
+ * two_sided = 1: both faces count; the term uses |s| and s = 0 gives 0.
+ * fov_deg in (0, 360): the target sees only a cone of half-angle fov/2
+ *   around the gaze axis a (Section III-B sets up the visible region as the
+ *   part of space inside the field of view, 120 degrees by default, Table II;
+ *   Section IV-C turns the gaze).  A patch p counts for q only when q lies in
+ *   p's cone.  The decision is a float32 computation that the GPU path makes
+ *   in the same way, so both take it identically:
+ *     c = (float) cos(fov_deg * pi / 360)            (double, then rounded)
+ *     a = (float) (g / |g|) per component             (double, then rounded;
+ *                                                      g = gaze, or n if 0)
+ *     r_k = q_k - p_k in float metres (k = x, y, z)
+ *     d = ((a_x r_x + a_y r_y) + a_z r_z), |d| if two-sided
+ *     rr = ((r_x r_x + r_y r_y) + r_z r_z)
+ *     inside  iff  d >= c * sqrt(rr)
+ *   with every operation a single float32 rounding (no fused multiply-add).
+ * Strict mode with a cone: 0 if any patch is blocked, else the sum over the
+ * patches inside the cone. */
 
 /* 0 on success, -1 on an invalid request. */
 int vo_check(const vo_scene *s, const vo_request *r);

@@ -11,7 +11,10 @@ Each group targets a plausible mistake:
     dropped cos, a wrong power of d, a wrong sign of the normal);
   * invariants: a full wall gives zero, adding boxes never clears a bit,
     mirror symmetry, viewpoints behind the target or inside a box give zero;
-  * colors: the quantiser's defining properties.
+  * colors: the quantiser's defining properties;
+  * sides and field of view: mirror images through the target plane and
+    through x = 0, a cone equal to a cropped target, the paper's FOV region
+    bounded by rays from the target ends.
 """
 
 import math
@@ -453,3 +456,182 @@ def test_viewer_mode_3d_square_solid_angle_and_blocking():
         assert bool(b[idx, 0]) == hit
         assert (v[idx] == 0.0) == hit
     assert b.any() and not b.all()
+
+
+# ---------------------------------------------------------------------------
+# two-sided target and field of view
+# ---------------------------------------------------------------------------
+
+FLAG_TWO_SIDED = 8
+
+
+def _mirror_y_scene(lo, hi):
+    mlo, mhi = lo.copy(), hi.copy()
+    mlo[:, 1], mhi[:, 1] = -hi[:, 1], -lo[:, 1]
+    return mlo, mhi
+
+
+def test_two_sided_front_equals_one_sided_and_back_mirrors_front():
+    """A target in the plane y = 0: from the front a two-sided target gives
+    exactly the one-sided values; from behind it gives exactly what the
+    mirror image (y -> -y, scene mirrored too) gives from the front; on the
+    plane it gives 0."""
+    rng = np.random.default_rng(21)
+    n = 50
+    lo = rng.integers(-90 * U, 80 * U, size=(n, 3))
+    lo[:, 2] = 0
+    hi = lo + rng.integers(2 * U, 14 * U, size=(n, 3))
+    keep = ~((lo[:, 0] < 12 * U) & (hi[:, 0] > -12 * U) & (lo[:, 1] < 2 * U) & (hi[:, 1] > -2 * U))
+    lo, hi = lo[keep], hi[keep]
+    sc = scene(3, list(zip(lo.tolist(), hi.tolist())))
+    mlo, mhi = _mirror_y_scene(lo, hi)
+    msc = scene(3, list(zip(mlo.tolist(), mhi.tolist())))
+    nx, ny = 8, 9
+    # rows iy = 0..8 at y = -64, -48, ..., 64 m: row 4 lies in the target plane
+    base = dict(width=12 * U, height=6 * U, pu=6, pw=3, origin=(-nx * 8 * U, -72 * U),
+                step=(16 * U, 16 * U), n=(nx, ny), layers=(2 * U, 15 * U))
+    one = O.run(sc, req3((0, 0, 20 * U), **base))
+    two = O.run(sc, req3((0, 0, 20 * U), flags=FLAG_TWO_SIDED, **base))
+    two_m = O.run(msc, req3((0, 0, 20 * U), flags=FLAG_TWO_SIDED, **base))
+    for layer in range(2):
+        for iy in range(ny):
+            for ix in range(nx):
+                i = (layer * ny + iy) * nx + ix
+                j = (layer * ny + (ny - 1 - iy)) * nx + ix
+                if iy > 4:
+                    assert two[i] == one[i]
+                elif iy == 4:
+                    assert two[i] == 0.0 and one[i] == 0.0
+                else:
+                    assert one[i] == 0.0
+                    assert two[i] == two_m[j]
+    assert (two[: nx * 4] > 0).any() and (two[nx * 5: nx * ny] > 0).any()
+
+
+def test_two_sided_2d_from_behind_converges_to_subtended_angle():
+    q_m = (3.0, -7.0)
+    W = 10.0
+    prev = None
+    for N in (64, 128, 256):
+        r = single_viewpoint(req2((0, 0), width=int(W * U), pu=N, flags=FLAG_TWO_SIDED),
+                             (int(q_m[0] * U), int(q_m[1] * U), 0))
+        v = O.run(scene(2, []), r)[0]
+        exact = _subtended_2d(q_m, (-W / 2, 0.0), (W / 2, 0.0))
+        err = abs(v - exact)
+        assert err < 2e-3 * exact
+        if prev is not None:
+            assert 3.0 < prev / err < 5.0
+        prev = err
+
+
+def _fov(req, fov, gaze=(0.0, 0.0, 0.0)):
+    r = dict(req)
+    r["fov_deg"] = fov
+    r["gaze"] = list(gaze)
+    return r
+
+
+def test_fov_none_full_and_half_space_equal_no_cone():
+    import synth
+    sc, r = synth.workload_3d(seed=13, grid=12, layers=2, patches=(8, 4), n_boxes=60, half_m=150.0,
+                              n_components=3, sigma_m=(20.0, 60.0))
+    v = O.run(sc, r)
+    for fov in (0.0, 360.0, 400.0, 180.0):
+        assert np.array_equal(O.run(sc, _fov(r, fov)), v)
+    # gaze along the normal, given explicitly or scaled, is the default axis
+    assert np.array_equal(O.run(sc, _fov(r, 100.0, (0.0, 1.0, 0.0))), O.run(sc, _fov(r, 100.0)))
+    assert np.array_equal(O.run(sc, _fov(r, 100.0, (0.0, 3.5, 0.0))), O.run(sc, _fov(r, 100.0)))
+
+
+def test_fov_equals_cropped_target():
+    """Seen from a point on the target's axis, a cone that takes exactly the
+    K middle patches (its edge falls between patch directions) gives the
+    value of a target cropped to those K patches, which has the same patch
+    centres."""
+    N, L = 32, 16 * U          # 32 patches of 0.5 m
+    D = 20.0
+    q = (0, int(D * U), 0)
+    for K in (2, 8, 20, 30):
+        # the half-angle between patch K/2 - 1/2 and K/2 + 1/2 half-widths off axis
+        x_in, x_out = (K / 2 - 0.5) * 0.5, (K / 2 + 0.5) * 0.5
+        half = 0.5 * (math.atan2(x_in, D) + math.atan2(x_out, D))
+        full = single_viewpoint(req2((0, 0), width=L, pu=N), q)
+        crop = single_viewpoint(req2((0, 0), width=K * L // N, pu=K), q)
+        v_cone = O.run(scene(2, []), _fov(full, math.degrees(2 * half)))[0]
+        v_crop = O.run(scene(2, []), crop)[0]
+        assert v_cone == pytest.approx(v_crop, rel=1e-14)
+
+
+def test_fov_monotone_and_mirror_symmetric():
+    rng = np.random.default_rng(8)
+    n = 40
+    lo = rng.integers(-80 * U, 70 * U, size=(n, 3))
+    lo[:, 1] = rng.integers(3 * U, 80 * U, size=n)
+    lo[:, 2] = 0
+    hi = lo + rng.integers(2 * U, 12 * U, size=(n, 3))
+    sc = scene(3, list(zip(lo.tolist(), hi.tolist())))
+    mlo, mhi = lo.copy(), hi.copy()
+    mlo[:, 0], mhi[:, 0] = -hi[:, 0], -lo[:, 0]
+    msc = scene(3, list(zip(mlo.tolist(), mhi.tolist())))
+    nx, ny = 10, 6
+    r = req3((0, 0, 20 * U), width=12 * U, height=6 * U, pu=6, pw=3, origin=(-nx * 8 * U, 4 * U),
+             step=(16 * U, 16 * U), n=(nx, ny), layers=(2 * U, 25 * U))
+    prev = None
+    for fov in (20.0, 60.0, 120.0, 170.0, 180.0):
+        v = O.run(sc, _fov(r, fov))
+        if prev is not None:
+            assert np.all(v >= prev)
+        prev = v
+    assert (prev > 0).sum() > (O.run(sc, _fov(r, 20.0)) > 0).sum()
+    gaze = (0.4, 1.0, -0.3)
+    v = O.run(sc, _fov(r, 90.0, gaze))
+    mv = O.run(msc, _fov(r, 90.0, (-gaze[0], gaze[1], gaze[2])))
+    for layer in range(2):
+        for iy in range(ny):
+            for ix in range(nx):
+                i = (layer * ny + iy) * nx + ix
+                j = (layer * ny + iy) * nx + (nx - 1 - ix)
+                assert v[i] == pytest.approx(mv[j], rel=1e-13, abs=0)
+    assert (v > 0).any()
+
+
+def test_fov_region_of_the_paper_is_bounded_by_rays_from_the_target_ends():
+    """With a 120 degree field of view the region from which the target is
+    seen at all is bounded by rays from its two end points at 60 degrees
+    from the normal (Section III-B).  Past the end T_B = (5, 0): a point at
+    70 degrees from the normal, seen from T_B, sees nothing; at 50 degrees it
+    sees the patches near T_B."""
+    r = req2((0, 0), width=10 * U, pu=64)
+    for ang, seen in ((70.0, False), (50.0, True)):
+        d = 40.0
+        q = (5.0 + d * math.sin(math.radians(ang)), d * math.cos(math.radians(ang)))
+        rq = single_viewpoint(_fov(r, 120.0), (round(q[0] * U), round(q[1] * U), 0))
+        v = O.run(scene(2, []), rq)[0]
+        assert (v > 0) == seen
+        # and no cone at all sees it either way
+        assert O.run(scene(2, []), single_viewpoint(r, (round(q[0] * U), round(q[1] * U), 0)))[0] > 0
+
+
+def test_fov_with_strict_mode_and_two_sided():
+    """Strict with a cone: 0 as soon as any patch is blocked, else the sum
+    over the patches in the cone; a two-sided cone is symmetric through the
+    target plane."""
+    sc = scene(3, [((-30 * U, 20 * U, 0), (-25 * U, 24 * U, 40 * U))])
+    base = dict(width=12 * U, height=6 * U, pu=6, pw=3, origin=(-64 * U, -60 * U), step=(16 * U, 15 * U),
+                n=(8, 9), layers=(5 * U,))
+    part = O.run(sc, _fov(req3((0, 0, 20 * U), **base), 100.0))
+    strict, bits = O.run(sc, _fov(req3((0, 0, 20 * U), flags=2 | 1, **base), 100.0), bits=True)
+    for i in range(part.shape[0]):
+        if bits[i].any():
+            assert strict[i] == 0.0
+        else:
+            assert strict[i] == part[i]
+    assert (strict > 0).any() and (bits.any(axis=1) & (part > 0)).any()
+    two = O.run(scene(3, []), _fov(req3((0, 0, 20 * U), flags=FLAG_TWO_SIDED, **base), 100.0))
+    nx, ny = 8, 9
+    ys = [-60 * U + 15 * U * iy + 15 * U // 2 for iy in range(ny)]   # row y, units
+    for iy in range(ny):
+        for iy2 in range(ny):
+            if ys[iy] == -ys[iy2] and ys[iy] != 0:
+                for ix in range(nx):
+                    assert two[iy * nx + ix] == two[iy2 * nx + ix]
