@@ -50,6 +50,15 @@ def peaks():
         return {}
 
 
+def hbm_peak():
+    """Copy bandwidth measured on the GB300s, else the recipe's
+    fallback figure."""
+    v = peaks().get("hbm_gbs")
+    if v:
+        return {"value": float(v), "basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    return {"value": 6800.0, "basis": "fallback 6.8 TB/s (no measured peak file)"}
+
+
 PROFILE = os.path.join(ROOT, "profiles", "k_tiles_3d_512x512x5_5000boxes.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_1310_7297_gb300", "csrc", "vcm_kernels.cu")
 
@@ -589,6 +598,94 @@ def run_large(args):
     ctx.close()
 
 
+def run_gaze(args):
+    """Incremental gaze change on the 3D workload (512 x 512 x 5 viewpoints,
+    5,000 boxes, 32 x 16 patches): occlusion bits once, then one recolour per
+    gaze direction (a 120 degree field of view turned in steps around the
+    vertical) against a full recompute with the same gaze.  The recolour
+    kernel reads ceil(P/32) words and writes one float per viewpoint; its
+    roofline is HBM."""
+    import math
+
+    import torch
+
+    import synth
+    from paper_1310_7297_gb300 import Context
+    from paper_1310_7297_gb300 import build as B
+    from paper_1310_7297_gb300.vcm import STATS_BYTES
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    scene, req = synth.workload_3d()
+    n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
+    P = req["patches_u"] * req["patches_w"]
+    words = (P + 31) // 32
+    ctx = Context(0)
+    ctx.load_scene(scene)
+    ctx.vcm_build(0.0)
+    stream = torch.cuda.current_stream(dev)
+    _, _, bits, _ = ctx.compute(req, emit_bits=True)
+    v = torch.empty(n_vp, dtype=torch.float32, device=dev)
+    c = torch.empty(n_vp, dtype=torch.uint8, device=dev)
+    st = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def gaze_req(k):
+        a = math.radians(-60.0 + 120.0 * k / max(1, args.steps - 1))
+        return dict(req, fov_deg=120.0, gaze=[math.sin(a), math.cos(a), 0.0])
+
+    for k in range(max(1, args.warmup)):
+        ctx.vcm_recolor(gaze_req(k), bits.data_ptr(), v.data_ptr(), c.data_ptr(), st.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ka = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for e in kb + ka:
+        e.record(stream)
+    torch.cuda.synchronize()
+    rec, kern, full = [], [], []
+    for k in range(args.steps):
+        r = gaze_req(k)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.vcm_set_timing_events(kb[k], ka[k])
+        a.record(stream)
+        ctx.vcm_recolor(r, bits.data_ptr(), v.data_ptr(), c.data_ptr(), st.data_ptr(), stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ctx.vcm_set_timing_events(None, None)
+        rec.append(a.elapsed_time(b))
+        kern.append(kb[k].elapsed_time(ka[k]))
+        flush.zero_()
+        a.record(stream)
+        ctx.vcm_compute(r, v.data_ptr(), c.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        full.append(a.elapsed_time(b))
+    k_ms = float(np.mean(kern))
+    # words are read for the viewpoints in front of the one-sided target only
+    # (the target faces req["normal"]); one float is written per viewpoint
+    ax, sgn = req["normal"] >> 1, (-1 if req["normal"] & 1 else 1)
+    coords = [(req["grid_origin"][k] + (np.arange(n) + 0.5) * req["grid_step"][k]) for k, n in
+              ((0, req["grid_nx"]), (1, req["grid_ny"]))] + [np.asarray(req["layer_z"], np.float64)]
+    per_axis = [req["grid_nx"], req["grid_ny"], len(req["layer_z"])]
+    n_front = int(np.sum(sgn * (coords[ax] - req["center"][ax]) > 0)) * n_vp // per_axis[ax]
+    bytes_per_launch = n_front * 4 * words + n_vp * 4
+    peak = hbm_peak()
+    achieved = bytes_per_launch / (k_ms / 1e3) / 1e9
+    out = {"mode": "gaze", "workload": "3D plain VCM 512x512x5, 5,000 boxes, 32x16 patches; 120 degree field of "
+                                      "view turned over 120 degrees in %d steps" % args.steps,
+           "recolor_ms": float(np.mean(rec)), "full_recompute_ms": float(np.mean(full)),
+           "speedup": float(np.mean(full)) / float(np.mean(rec)),
+           "cells_per_s": n_vp / (float(np.mean(rec)) / 1e3),
+           "roofline": {"bound": "hbm", "kernel": "k_recolor", "achieved": achieved, "peak": peak["value"],
+                        "unit": "GB/s", "frac": achieved / peak["value"], "peak_basis": peak["basis"],
+                        "bytes_per_launch": bytes_per_launch, "front_viewpoints": n_front, "kernel_ms": k_ms,
+                        "traffic": None},
+           "l2": "512 MB buffer written between timed calls"}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -597,9 +694,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "batched", "serve", "large"], default="step",
+    ap.add_argument("--mode", choices=["step", "batched", "serve", "large", "gaze"], default="step",
                     help="step: the timed VCM step (default); batched / serve: the batching and serving runs; "
-                         "large: the 100,000-box scene at full size")
+                         "large: the 100,000-box scene at full size; gaze: recolouring for new gazes")
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=400)
@@ -616,6 +713,8 @@ def main():
         run_serve(args)
     elif args.mode == "large":
         run_large(args)
+    elif args.mode == "gaze":
+        run_gaze(args)
     else:
         run_gpu(args)
 

@@ -84,8 +84,12 @@ enum { VCM_AXIS_PX = 0, VCM_AXIS_NX = 1, VCM_AXIS_PY = 2, VCM_AXIS_NY = 3,
  *                S x S square, 4 asin(S^2 / (S^2 + 4 D^2)) (3D), with D the
  *                distance to the viewer, or 0 if the segment from the cell to
  *                the viewer meets a box (or D = 0).  Axes, height and patch
- *                counts are ignored; bits (one per cell) mark blocked cells. */
-enum { VCM_EMIT_BITS = 1u, VCM_STRICT = 2u, VCM_VIEWER = 4u };
+ *                counts are ignored; bits (one per cell) mark blocked cells.
+ * VCM_TWO_SIDED: the target counts from both of its faces: a patch's term
+ *                uses |n.(q - p)| instead of requiring n.(q - p) > 0, so
+ *                viewpoints behind the target are measured too (viewpoints
+ *                in its plane still get 0).  Not with VCM_VIEWER. */
+enum { VCM_EMIT_BITS = 1u, VCM_STRICT = 2u, VCM_VIEWER = 4u, VCM_TWO_SIDED = 8u };
 
 #define VCM_UNITS_PER_M 1024
 #define VCM_COORD_LIMIT_M 16384.0f
@@ -116,7 +120,24 @@ typedef struct {
     const float *layer_z;    /* host pointer, n_layers heights; copied */
     uint32_t color_levels;   /* L, 2..256 */
     float v_ref;             /* > 0: normalise by this; <= 0: by the largest v */
-    uint32_t flags;          /* VCM_EMIT_BITS */
+    uint32_t flags;          /* VCM_EMIT_BITS | VCM_STRICT | VCM_VIEWER | VCM_TWO_SIDED */
+    /* Field of view of the target (Section III-B: the visible region starts
+     * as the part of space inside the FOV, 120 degrees by default in
+     * Table II; Section IV-C turns the gaze).  fov_deg in (0, 360): patch p
+     * counts for viewpoint q only if q lies in p's cone of half-angle
+     * fov_deg / 2 around the axis `gaze` (world x, y, z; all 0 = the
+     * target's facing normal; z ignored in 2D).  0 or >= 360: no cone.  The
+     * test is a float32 computation with one rounding per operation, in
+     * this order, with r = q - p per world axis in metres:
+     *   c = (float) cos(fov_deg * pi / 360)        (in double, then rounded)
+     *   a = (float) (g / |g|) per component         (in double, then rounded)
+     *   d = (a.x r.x + a.y r.y) + a.z r.z, |d| with VCM_TWO_SIDED
+     *   inside iff d >= c * sqrt((r.x r.x + r.y r.y) + r.z r.z)
+     * In strict mode a viewpoint still gets 0 if any patch is blocked, and
+     * otherwise the sum over the patches inside the cone.  Not with
+     * VCM_VIEWER. */
+    float fov_deg;
+    float gaze[3];
 } vcm_request;
 
 /* Per-request counters written by the device. */
@@ -283,12 +304,36 @@ vcm_status vcm_compute_static(const float *lo, const float *hi, uint32_t n_boxes
                               const vcm_request *req, float *d_v, uint8_t *d_color, uint32_t *d_bits,
                               vcm_stats *d_stats, void *stream);
 
+/* ---- incremental gaze change ------------------------------------------ */
+
+/* Recolour a target-centric request from occlusion bits made earlier, with
+ * no occlusion test (Section IV-C: when the gaze turns, only the field of
+ * view changes, so the work done once for every direction is reused).  A
+ * request's occlusion bits do not depend on its field of view, gaze, sides
+ * or strictness.  So one vcm_compute with VCM_EMIT_BITS serves every later
+ * gaze: `req` must describe the same target, patch counts and viewpoint
+ * grid as that computation, while its fov_deg, gaze, VCM_TWO_SIDED,
+ * VCM_STRICT, color_levels and v_ref may differ (VCM_EMIT_BITS is ignored;
+ * VCM_VIEWER is rejected with VCM_E_ARG).  The result equals what
+ * vcm_compute would give for `req`.
+ *
+ * d_bits: device, n_viewpoints x ceil(P/32) words as VCM_EMIT_BITS wrote
+ * them (read only).  d_v (n_viewpoints floats), d_color (n_viewpoints bytes,
+ * or NULL) and d_stats (one vcm_stats; slab_tests and corner_tests stay 0):
+ * caller-owned device outputs.  At most 2^31 - 1 viewpoints.  Enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default); needs no scene.  The
+ * context keeps n_viewpoints ints of device scratch (grown on demand).  The caller keeps d_bits unchanged
+ * until the work has run.  The call uses the context's descriptor buffer
+ * and so is serialised with vcm_compute on the same context. */
+vcm_status vcm_recolor(vcm_ctx *ctx, const vcm_request *req, const uint32_t *d_bits, float *d_v,
+                       uint8_t *d_color, vcm_stats *d_stats, void *stream);
+
 /* ---- profiling --------------------------------------------------------- */
 
 /* Record two caller-created CUDA events (cudaEvent_t) on the launch stream
  * immediately before and after the tile kernel of every later direct-path
- * launch (vcm_compute, vcm_compute_batch); NULL, NULL stops.  The events
- * must outlive their use. */
+ * launch (vcm_compute, vcm_compute_batch) and the recolour kernel of every
+ * later vcm_recolor; NULL, NULL stops.  The events must outlive their use. */
 vcm_status vcm_set_timing_events(vcm_ctx *ctx, void *before_tiles, void *after_tiles);
 
 #ifdef __cplusplus

@@ -7,6 +7,7 @@ include/vcm.h); ``vcm`` is its thin ctypes binding.  Build it with
 """
 
 from .vcm import (  # noqa: F401
-    VCM_EMIT_BITS, VCM_STRICT, VCM_VIEWER, Context, VcmError, lib, make_request, n_viewpoints, stats_from_tensor,
+    VCM_EMIT_BITS, VCM_STRICT, VCM_TWO_SIDED, VCM_VIEWER, Context, VcmError, lib, make_request, n_viewpoints,
+    stats_from_tensor,
     words,
 )

@@ -17,7 +17,10 @@ LIB = os.path.join(BUILD, "libvcm.so")
 SOURCES = ["vcm_kernels.cu", "vcm_api.cpp"]
 HEADERS = [os.path.join(CSRC, "vcm_internal.h"), os.path.join(ROOT, "include", "vcm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
+# Host code: no contraction into fused multiply-adds, so that host float
+# arithmetic (the field-of-view set-up) rounds every operation once.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+         "-Xcompiler", "-ffp-contract=off"]
 
 
 def nvcc():

@@ -54,6 +54,7 @@ vcm_status fail(vcm_status s, const char *fmt, ...)
 
 constexpr int64_t kLimitUnits = int64_t(1) << 24;
 constexpr double kUnitsPerM = 1024.0;
+constexpr double kPi = 3.14159265358979323846;
 
 bool to_units(float x, int64_t &u)
 {
@@ -100,6 +101,8 @@ struct Canon {
     int levels = 16;
     float v_ref = 0.f;
     unsigned flags = 0;
+    int cone = 0;
+    float cone_c = 0.f, cone_a[3] = {0.f, 0.f, 0.f};
     long long n_vp = 0;
     size_t out_bytes() const
     {
@@ -155,13 +158,24 @@ vcm_status canonicalise(const vcm_request *r, Canon &c)
     if (r->dims != 2 && r->dims != 3)
         return fail(VCM_E_ARG, "dims must be 2 or 3 (got %d)", r->dims);
     c.dims = r->dims;
-    if (r->flags & ~(uint32_t)(VCM_EMIT_BITS | VCM_STRICT | VCM_VIEWER))
+    if (r->flags & ~(uint32_t)(VCM_EMIT_BITS | VCM_STRICT | VCM_VIEWER | VCM_TWO_SIDED))
         return fail(VCM_E_ARG, "unknown flag bits 0x%x", r->flags);
     if ((r->flags & VCM_STRICT) && (r->flags & VCM_VIEWER))
         return fail(VCM_E_ARG, "VCM_STRICT and VCM_VIEWER exclude each other");
+    if ((r->flags & VCM_TWO_SIDED) && (r->flags & VCM_VIEWER))
+        return fail(VCM_E_ARG, "VCM_TWO_SIDED and VCM_VIEWER exclude each other");
+    if (!std::isfinite(r->fov_deg) || r->fov_deg < 0.f)
+        return fail(VCM_E_ARG, "fov_deg must be finite and >= 0");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(r->gaze[k]))
+            return fail(VCM_E_ARG, "gaze must be finite");
+    const bool cone = r->fov_deg > 0.f && r->fov_deg < 360.f;
     c.flags = r->flags;
-    if (r->flags & VCM_VIEWER)
+    if (r->flags & VCM_VIEWER) {
+        if (cone)
+            return fail(VCM_E_ARG, "a field of view applies to target-centric requests only");
         return canonicalise_viewer(r, c);
+    }
     if (r->axis_u < 0 || r->axis_u > 5 || r->normal < 0 || r->normal > 5)
         return fail(VCM_E_ARG, "axis codes must be 0..5");
     c.au = r->axis_u >> 1;
@@ -182,6 +196,17 @@ vcm_status canonicalise(const vcm_request *r, Canon &c)
             return fail(VCM_E_ARG, "2D target: axis_u and normal must be x and y in some order");
     }
     c.perm = perm_index(c.au, c.an, c.aw);
+    if (cone) {
+        // the cone's cosine and unit axis, rounded once from double
+        c.cone = 1;
+        c.cone_c = (float)std::cos((double)r->fov_deg * kPi / 360.0);
+        double g[3] = {r->gaze[0], r->gaze[1], c.dims == 3 ? r->gaze[2] : 0.0f};
+        if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0)
+            g[c.an] = (double)c.sn;
+        const double len = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        for (int k = 0; k < 3; ++k)
+            c.cone_a[k] = (float)(g[k] / len);
+    }
     if (r->patches_u < 1 || r->patches_u > VCM_MAX_PATCHES_SIDE)
         return fail(VCM_E_ARG, "patches_u must be 1..%u", VCM_MAX_PATCHES_SIDE);
     c.nu = (int)r->patches_u;
@@ -304,6 +329,8 @@ void fill_shape(const Canon &c, const vcm_tune &t, DevRequest &d)
     int k = pow2_at_least(std::min(rows_per_lane, 8));
     if (t.patch_k > 0)
         k = std::min(k, pow2_at_least(std::min<int>(t.patch_k, 8)));
+    if (c.cone || (c.flags & VCM_TWO_SIDED))
+        k = 8;   // the tile kernel sweeps these requests with its 8-row variant
     d.k_rows = k;
     d.row_passes = (c.nw + d.groups * k - 1) / (d.groups * k);
     d.tile_x = (int)std::max(1u, t.tile_x);
@@ -452,6 +479,9 @@ struct vcm_ctx {
     std::vector<std::unique_ptr<Slot>> slots;   // scheduler
     uint32_t max_batch = 64;
     cudaEvent_t ev_before = nullptr, ev_after = nullptr;   // optional timing of the tile kernel
+    int *d_recolor_list = nullptr;   // vcm_recolor: viewpoints that need a measure, and their count
+    int *d_recolor_n = nullptr;
+    size_t recolor_cap = 0;
     PinnedPool pinned;
     cudaStream_t aux = nullptr;
     // scheduler
@@ -496,7 +526,7 @@ vcm_tune default_tune()
     t.tile_x = 16;
     t.tile_y = 8;
     t.patch_k = 8;
-    t.box_cap = 1024;
+    t.box_cap = 512;
     return t;
 }
 
@@ -573,6 +603,10 @@ void fill_desc(char *h, const char *d_base, const Layout &L, const std::vector<c
         d.levels = c.levels;
         d.flags = c.flags;
         d.box_cap = box_cap;
+        d.cone = c.cone;
+        d.cone_c = c.cone_c;
+        for (int k = 0; k < 3; ++k)
+            d.cone_a[k] = c.cone_a[k];
         reqs[i] = d;
         tiles[i] = tp;
         vps[i] = vp;
@@ -651,7 +685,7 @@ int launch_box_cap(const std::vector<vcm_tune> &shapes)
 
 int grid_blocks_for(vcm_ctx *ctx, int box_cap, int total_tiles)
 {
-    const int per_sm = tiles_blocks_per_sm(box_cap, 16);
+    const int per_sm = tiles_blocks_per_sm(box_cap);
     return std::max(1, std::min(total_tiles, per_sm * ctx->sm_count));
 }
 
@@ -660,7 +694,11 @@ struct Prepared {
     int box_cap = 0;
     int blocks = 0;
     size_t n = 0;
+    bool extra = false;   // a request is two-sided or has a field-of-view cone
+    bool any_bits = false;   // a request emits occlusion bits
 };
+
+bool needs_extra(const Canon &c) { return c.cone || (c.flags & VCM_TWO_SIDED); }
 
 // Host half of a launch: layout, scratch, and the descriptor arena filled in
 // pinned memory.  `stats` must hold cs.size() entries.
@@ -674,6 +712,11 @@ vcm_status prepare_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *
     P.box_cap = launch_box_cap(shapes);
     P.blocks = grid_blocks_for(ctx, P.box_cap, P.L.total_tiles);
     P.n = cs.size();
+    P.extra = P.any_bits = false;
+    for (const Canon *c : cs) {
+        P.extra = P.extra || needs_extra(*c);
+        P.any_bits = P.any_bits || (c->flags & VCM_EMIT_BITS);
+    }
     vcm_status st = ensure_slot(ctx, s, P.L.bytes, cs.size(), P.blocks, sync_stream);
     if (st != VCM_OK)
         return st;
@@ -694,16 +737,16 @@ vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *st
     // a captured launch records it after the graph launch instead.
     if (!capturing)
         CUDA_TRY(cudaEventRecord(s.desc_copied, stream));
-    CUDA_TRY(cudaMemsetAsync(s.d_work, 0, sizeof(int), stream));
-    CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(vcm_stats) * P.n, stream));
+
     const DevRequest *d_reqs = reinterpret_cast<const DevRequest *>(s.d_desc + P.L.off_reqs);
     const int *d_tiles = reinterpret_cast<const int *>(s.d_desc + P.L.off_tiles);
     const long long *d_vps = reinterpret_cast<const long long *>(s.d_desc + P.L.off_vps);
-    CUDA_TRY(launch_zero_bits(d_reqs, (int)P.n, stream));
+    (void)stats;   // the descriptors point into it; the prologue clears it
+    CUDA_TRY(launch_prologue(d_reqs, (int)P.n, s.d_work, P.any_bits, stream));
     if (timed && ctx->ev_before)
         CUDA_TRY(cudaEventRecord(ctx->ev_before, stream));
     CUDA_TRY(launch_tiles(ctx->scene, d_reqs, d_tiles, (int)P.n, P.L.total_tiles, s.d_work, s.d_spill,
-                          P.blocks, P.box_cap, 16, stream, one_tile, s.d_spill_busy));
+                          P.blocks, P.box_cap, P.extra, stream, one_tile, s.d_spill_busy));
     if (timed && ctx->ev_after)
         CUDA_TRY(cudaEventRecord(ctx->ev_after, stream));
     CUDA_TRY(launch_quantise(d_reqs, d_vps, (int)P.n, P.L.total_vp, stream));
@@ -788,6 +831,8 @@ void free_scene(vcm_ctx *ctx)
     cudaFree(ctx->d_cell_lo);
     cudaFree(ctx->d_cell_hi);
     cudaFree(ctx->d_overhang);
+    cudaFree(ctx->d_recolor_list);
+    cudaFree(ctx->d_recolor_n);
     ctx->d_cell_start = ctx->d_cell_of = ctx->d_count = ctx->d_cursor = ctx->d_order = nullptr;
     ctx->d_cell_lo = ctx->d_cell_hi = nullptr;
     ctx->d_overhang = nullptr;
@@ -1641,6 +1686,65 @@ vcm_status vcm_get_tune(vcm_ctx *ctx, const vcm_request *req, vcm_tune *out)
     return VCM_OK;
 }
 
+vcm_status vcm_recolor(vcm_ctx *ctx, const vcm_request *req, const uint32_t *d_bits, float *d_v,
+                       uint8_t *d_color, vcm_stats *d_stats, void *stream)
+{
+    try {
+        vcm_status st = validate_ctx(ctx);
+        if (st != VCM_OK)
+            return st;
+        if (!d_bits || !d_v || !d_stats)
+            return fail(VCM_E_ARG, "d_bits, d_v and d_stats are required");
+        Canon c;
+        if ((st = canonicalise(req, c)) != VCM_OK)
+            return st;
+        if (c.flags & VCM_VIEWER)
+            return fail(VCM_E_ARG, "vcm_recolor takes target-centric requests only");
+        c.flags &= ~(unsigned)VCM_EMIT_BITS;   // the bits are an input here
+        if (c.n_vp > (long long)INT32_MAX)
+            return fail(VCM_E_ARG, "vcm_recolor takes at most 2^31 - 1 viewpoints");
+        const std::vector<const Canon *> cs{&c};
+        const std::vector<vcm_tune> shapes{default_tune()};
+        const cudaStream_t strm = static_cast<cudaStream_t>(stream);
+        std::lock_guard<std::mutex> g(ctx->mu);
+        Slot &s = ctx->direct;
+        const Layout L = layout_for(cs, shapes);
+        if ((st = ensure_slot(ctx, s, L.bytes, 1, 1, strm)) != VCM_OK)
+            return st;
+        // the previous upload from the pinned descriptors must have completed
+        CUDA_TRY(cudaEventSynchronize(s.desc_copied));
+        if ((size_t)c.n_vp > ctx->recolor_cap) {
+            // earlier work may still read the old list
+            CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(ctx->d_recolor_list);
+            ctx->d_recolor_list = nullptr;
+            ctx->recolor_cap = 0;
+            CUDA_TRY(cudaMalloc(&ctx->d_recolor_list, sizeof(int) * (size_t)c.n_vp));
+            ctx->recolor_cap = (size_t)c.n_vp;
+        }
+        if (!ctx->d_recolor_n)
+            CUDA_TRY(cudaMalloc(&ctx->d_recolor_n, sizeof(int)));
+        float *vv[1] = {d_v};
+        uint8_t *cc[1] = {d_color};
+        uint32_t *bb[1] = {const_cast<uint32_t *>(d_bits)};   // read only in k_recolor
+        fill_desc(s.h_desc, s.d_desc, L, cs, shapes, vv, cc, bb, d_stats, 256);
+        CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, L.bytes, cudaMemcpyHostToDevice, strm));
+        CUDA_TRY(cudaEventRecord(s.desc_copied, strm));
+        CUDA_TRY(cudaMemsetAsync(d_stats, 0, sizeof(vcm_stats), strm));
+        const DevRequest *d_reqs = reinterpret_cast<const DevRequest *>(s.d_desc + L.off_reqs);
+        const long long *d_vps = reinterpret_cast<const long long *>(s.d_desc + L.off_vps);
+        if (ctx->ev_before)
+            CUDA_TRY(cudaEventRecord(ctx->ev_before, strm));
+        CUDA_TRY(launch_recolor(d_reqs, c.n_vp, ctx->sm_count, ctx->d_recolor_list, ctx->d_recolor_n, strm));
+        if (ctx->ev_after)
+            CUDA_TRY(cudaEventRecord(ctx->ev_after, strm));
+        CUDA_TRY(launch_quantise(d_reqs, d_vps, 1, c.n_vp, strm));
+        return VCM_OK;
+    } catch (const std::exception &ex) {
+        return fail(VCM_E_NOMEM, "vcm_recolor: %s", ex.what());
+    }
+}
+
 vcm_status vcm_compute_static(const float *lo, const float *hi, uint32_t n_boxes, int32_t dims,
                               const vcm_request *req, float *d_v, uint8_t *d_color, uint32_t *d_bits,
                               vcm_stats *d_stats, void *stream)
@@ -1765,17 +1869,16 @@ vcm_status vcm_compute_static(const float *lo, const float *hi, uint32_t n_boxes
         uint32_t *bb[1] = {d_bits};
         fill_desc(hdesc.data(), s_desc, lay, cs, shapes, vv, cc, bb, d_stats, (int)t.box_cap);
         CUDA_TRY(cudaMemcpyAsync(s_desc, hdesc.data(), lay.bytes, cudaMemcpyHostToDevice, sm));
-        CUDA_TRY(cudaMemsetAsync(s_work, 0, sizeof(int), sm));
-        CUDA_TRY(cudaMemsetAsync(d_stats, 0, sizeof(vcm_stats), sm));
         const DevRequest *d_reqs = reinterpret_cast<const DevRequest *>(s_desc + lay.off_reqs);
         const int *d_tiles = reinterpret_cast<const int *>(s_desc + lay.off_tiles);
         const long long *d_vps = reinterpret_cast<const long long *>(s_desc + lay.off_vps);
         int sm_count = 1, dev = 0;
         CUDA_TRY(cudaGetDevice(&dev));
         CUDA_TRY(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
-        const int blocks = std::max(1, std::min(lay.total_tiles, tiles_blocks_per_sm((int)t.box_cap, 16) * sm_count));
-        CUDA_TRY(launch_zero_bits(d_reqs, 1, sm));
-        CUDA_TRY(launch_tiles(sc, d_reqs, d_tiles, 1, lay.total_tiles, s_work, s_spill, blocks, (int)t.box_cap, 16, sm));
+        const int blocks = std::max(1, std::min(lay.total_tiles, tiles_blocks_per_sm((int)t.box_cap) * sm_count));
+        CUDA_TRY(launch_prologue(d_reqs, 1, s_work, (c.flags & VCM_EMIT_BITS) != 0, sm));
+        CUDA_TRY(launch_tiles(sc, d_reqs, d_tiles, 1, lay.total_tiles, s_work, s_spill, blocks, (int)t.box_cap,
+                              needs_extra(c), sm));
         CUDA_TRY(launch_quantise(d_reqs, d_vps, 1, lay.total_vp, sm));
         return VCM_OK;
     } catch (const std::exception &ex) {

@@ -12,6 +12,7 @@ namespace vcm {
 
 constexpr int kWarps = 4;                 // warps per block of the tile kernel
 constexpr int kThreads = kWarps * 32;
+constexpr int kPassCap = 2 * kThreads;       // cells listed per round of the grid walk
 constexpr int kMaxPlanes = 32;            // separating planes kept per tile hull
 constexpr float kBand = 1e-6f;            // FP32 slab margin re-decided in FP64
 constexpr int kMaxBoxCap = 5000;          // candidate boxes a tile stages in shared memory
@@ -65,6 +66,9 @@ struct DevRequest {
     int levels;
     unsigned flags;
     int box_cap;               // candidate boxes staged in shared memory
+    int cone;                  // 1: a field-of-view cone masks the patches
+    float cone_c;              // cosine of its half-angle
+    float cone_a[3];           // its unit axis, world x, y, z
 };
 
 // Launch helpers implemented in vcm_kernels.cu.  All are asynchronous on
@@ -83,21 +87,30 @@ cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, 
 // blocks that can be resident at once, and `d_spill_busy` (grid_blocks ints,
 // all zero between launches) hands out the spill regions.  `d_spill` holds
 // grid_blocks * n_boxes ints for candidate lists longer than box_cap.
+// `extra` must be set when any request is two-sided or has a field-of-view
+// cone: it selects the tile kernel's instantiation that handles them.
 cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
                          int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
-                         int box_cap, int k_rows_max, cudaStream_t stream, bool one_tile = false,
+                         int box_cap, bool extra, cudaStream_t stream, bool one_tile = false,
                          int *d_spill_busy = nullptr);
-
 // Colors and edge counts for all viewpoints of n_req requests (grid over the
 // concatenated viewpoints, `d_vp_prefix` = exclusive prefix, n_req + 1).
 cudaError_t launch_quantise(const DevRequest *d_reqs, const long long *d_vp_prefix, int n_req,
                             long long total_vp, cudaStream_t stream);
 
-// Zero the occlusion-bit buffers of requests with VCM_EMIT_BITS.
-cudaError_t launch_zero_bits(const DevRequest *d_reqs, int n_req, cudaStream_t stream);
+// Values of one request (d_req[0]) recomputed from the occlusion bits its
+// bits_out points at (read only); colors then come from launch_quantise.
+// d_list: n_vp ints of scratch for the viewpoints that need a measure, and
+// d_n_list their count (n_vp <= INT_MAX).
+cudaError_t launch_recolor(const DevRequest *d_req, long long n_vp, int sm_count, int *d_list, int *d_n_list,
+                           cudaStream_t stream);
+
+// Zero the tile-queue counter d_work, every request's vcm_stats and, when
+// any_bits, the occlusion-bit buffers of the requests with VCM_EMIT_BITS.
+cudaError_t launch_prologue(const DevRequest *d_reqs, int n_req, int *d_work, bool any_bits, cudaStream_t stream);
 
 // Blocks of the tile kernel that fit on one SM for this shared-memory size.
-int tiles_blocks_per_sm(int box_cap, int k_rows_max);
+int tiles_blocks_per_sm(int box_cap);
 
 // One-time per-device setup (constant tables, kernel attributes); must run
 // before any launch is captured into a graph.

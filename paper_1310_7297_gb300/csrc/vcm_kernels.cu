@@ -14,6 +14,7 @@
 #include "vcm_internal.h"
 
 #include <cfloat>
+#include <climits>
 #include <cstdio>
 #include <mutex>
 
@@ -477,7 +478,40 @@ __device__ __forceinline__ int pyramid_planes(const DevRequest &R, float qu, flo
 // only on the viewpoint and along w only on its row, so the u and n parts
 // of the slab test are formed once per box and column, and each row adds
 // its w interval.
-template <int K, bool MIXED>
+// Does a viewpoint at normal coordinate qn see the measured side of the
+// target?  One-sided: n.(q - p) > 0.  Two-sided: anywhere off its plane.
+__device__ __forceinline__ bool facing(const DevRequest &R, float qn)
+{
+    return (R.flags & VCM_TWO_SIDED) ? qn != R.p_n : R.sn * (qn - R.p_n) > 0.f;
+}
+
+// Field-of-view cone (Section III-B, Table II): is q inside the cone of the
+// patch at q - r?  r comes in target-frame components (u, n, w), each the
+// rounded float difference q - p; the test runs in world order x, y, z with
+// one float32 rounding per operation (no fused multiply-add), exactly as the
+// request header defines it, so every implementation of that definition
+// takes the same decisions.
+__device__ __forceinline__ bool in_cone_inline(const DevRequest &R, float ru, float rn, float rw)
+{
+    const float r0 = R.au == 0 ? ru : (R.an == 0 ? rn : rw);
+    const float r1 = R.au == 1 ? ru : (R.an == 1 ? rn : rw);
+    const float r2 = R.au == 2 ? ru : (R.an == 2 ? rn : rw);
+    float d = __fadd_rn(__fmul_rn(R.cone_a[0], r0), __fmul_rn(R.cone_a[1], r1));
+    d = __fadd_rn(d, __fmul_rn(R.cone_a[2], r2));
+    if (R.flags & VCM_TWO_SIDED)
+        d = fabsf(d);
+    float rr = __fadd_rn(__fmul_rn(r0, r0), __fmul_rn(r1, r1));
+    rr = __fadd_rn(rr, __fmul_rn(r2, r2));
+    return d >= __fmul_rn(R.cone_c, __fsqrt_rn(rr));
+}
+
+// The same, not inlined, for the tile kernel's sweep (keeps its code small).
+__device__ __noinline__ bool in_cone(const DevRequest &R, float ru, float rn, float rw)
+{
+    return in_cone_inline(R, ru, rn, rw);
+}
+
+template <int K, bool MIXED, bool EXTRA>
 __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const float4 *__restrict__ sbox,
                                                  int n_smem, const int *__restrict__ spill, int count,
                                                  const float4 *__restrict__ gbox, float qu, float qn,
@@ -509,7 +543,8 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
         const bool sgn_u = du >= 0.f;
         const float ru = qu - pu, rn = qn - R.p_n;
         const float col_d2 = fmaf(ru, ru, rn * rn);
-        const float m_s = R.measure * (R.sn * rn);   // measure x |r| cos(theta)
+        // measure x |r| cos(theta); a two-sided target is measured from either side
+        const float m_s = R.measure * ((EXTRA && (R.flags & VCM_TWO_SIDED)) ? fabsf(rn) : R.sn * rn);
         for (int rp = 0; rp < R.row_passes && !(strict_exit && strict_fail); ++rp) {
             float inv_w[K], clampv[K];
             unsigned valid = 0, sgnw = 0;
@@ -632,6 +667,8 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                     } else if (front) {
                         // |r|^2 = (ru^2 + rn^2) of the column + rw^2 of the row
                         const float rw = qw - w_coord[iw];
+                        if (EXTRA && R.cone && !in_cone(R, ru, rn, rw))
+                            continue;   // q is outside this patch's field of view
                         const float d2 = fmaf(rw, rw, col_d2);
                         float term;
                         if (R.dims == 3) {
@@ -715,12 +752,33 @@ __device__ __forceinline__ float sweep_k(const DevRequest &R, const float4 *sbox
 {
     const bool mixed = !(qw <= R.w_min) && !(qw > R.w_max);
     if (mixed)
-        return sweep_viewpoint<K, true>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr,
-                                        npyr, tests, rechecks);
-    return sweep_viewpoint<K, false>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr,
-                                     tests, rechecks);
+        return sweep_viewpoint<K, true, false>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr,
+                                               npyr, tests, rechecks);
+    return sweep_viewpoint<K, false, false>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr,
+                                            npyr, tests, rechecks);
 }
 
+// Cull one box against the hull planes and, if it may matter, add it to the
+// tile's candidate list (shared memory, then the block's spill region).
+__device__ __forceinline__ void add_candidate(const float4 *__restrict__ world, const Plane *planes, int n_planes,
+                                              int s, TileSmem &sm, int *s_ids, int box_cap, int *spill,
+                                              int spill_slot, const DevRequest &R)
+{
+    if (outside(planes, n_planes, world[2 * s], world[2 * s + 1]))
+        return;
+    const int pos = atomicAdd(&sm.count, 1);
+    if (pos < box_cap)
+        s_ids[pos] = s;
+    else if (spill_slot >= 0)
+        spill[pos - box_cap] = s;
+    else
+        R.stats->error = 2u;   // no spill region: the result is flagged
+}
+
+// EXTRA: the instantiation for launches that hold a two-sided or cone
+// request; the common one carries none of that code (the tile kernel is
+// sensitive to its instruction footprint).
+template <bool EXTRA>
 __global__ void __launch_bounds__(kThreads, 4)
 k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict__ tile_prefix,
         int n_req, int total_tiles, int *__restrict__ work, int *__restrict__ spill_all, int box_cap,
@@ -738,11 +796,13 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
     __shared__ int s_next2;                     // cursor of the undecided list
     __shared__ int s_und[kMaxTileViewpoints];   // viewpoints left by the one-box check
     __shared__ int s_rowpre[kThreads], s_rowx[kThreads], s_wsum[kWarps];   // cell-row spans
+    __shared__ int s_passb[kPassCap], s_passn[kPassCap], s_passp[kPassCap + 1], s_wsum2[kWarps], s_npass;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     __shared__ int s_spill_slot;
     if (tid == 0) {
         s_req_idx = -1;
+        s_npass = 0;
         sm.item = -1;
         // A persistent block owns spill region blockIdx.x.  A one-tile block
         // claims a free region for the length of its tile.  There are as
@@ -855,7 +915,8 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             qn_lo = R.y_coord[iy0]; qn_hi = R.y_coord[iy1 - 1];
         }
         const bool viewer = (R.flags & VCM_VIEWER) != 0;
-        const bool any_front = viewer || (R.sn > 0.f ? (qn_hi - R.p_n > 0.f) : (R.p_n - qn_lo > 0.f));
+        const bool any_front = viewer || (R.flags & VCM_TWO_SIDED) ||
+                               (R.sn > 0.f ? (qn_hi - R.p_n > 0.f) : (R.p_n - qn_lo > 0.f));
         if (!any_front && !want_bits) {
             for (int i = tid; i < tn; i += kThreads) {
                 const int ix = ix0 + i % tw, iy = iy0 + i / tw;
@@ -952,6 +1013,8 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 s_rowpre[tid] = before + incl - width;
                 s_rowx[tid] = xa;
                 __syncthreads();
+                // (a) threads over cells: the cells whose bounds meet the
+                // hull are listed (box range start and length)
                 for (int c = tid; c < total; c += kThreads) {
                     // the row of cell c: the last t with s_rowpre[t] <= c
                     int t = 0;
@@ -963,18 +1026,67 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                     const int b = sc.cell_start[cell], e = sc.cell_start[cell + 1];
                     if (b == e || outside(sm.planes, n_planes, sc.cell_lo[cell], sc.cell_hi[cell]))
                         continue;
-                    for (int s = b; s < e; ++s) {
-                        if (outside(sm.planes, n_planes, world[2 * s], world[2 * s + 1]))
-                            continue;
-                        const int pos = atomicAdd(&sm.count, 1);
-                        if (pos < box_cap)
-                            s_ids[pos] = s;
-                        else if (spill_slot >= 0)
-                            spill[pos - box_cap] = s;
-                        else
-                            R.stats->error = 2u;   // no spill region: the result is flagged
+                    const int k = atomicAdd(&s_npass, 1);
+                    if (k < kPassCap) {
+                        s_passb[k] = b;
+                        s_passn[k] = e - b;
+                        continue;
                     }
+                    for (int s = b; s < e; ++s)   // list full: this cell's boxes here
+                        add_candidate(world, sm.planes, n_planes, s, sm, s_ids, box_cap, spill, spill_slot, R);
                 }
+                __syncthreads();
+                // (b) exclusive scan of the listed cells' box counts
+                const int n_pass = min(s_npass, kPassCap);
+                {
+                    int cnt[kPassCap / kThreads], local = 0;
+#pragma unroll
+                    for (int q = 0; q < kPassCap / kThreads; ++q) {
+                        const int k = tid * (kPassCap / kThreads) + q;
+                        cnt[q] = k < n_pass ? s_passn[k] : 0;
+                        local += cnt[q];
+                    }
+                    int incl = local;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int t = __shfl_up_sync(kFull, incl, off);
+                        if (lane >= off)
+                            incl += t;
+                    }
+                    if (lane == 31)
+                        s_wsum2[warp] = incl;
+                    __syncthreads();
+                    int run = 0, all = 0;
+#pragma unroll
+                    for (int w2 = 0; w2 < kWarps; ++w2) {
+                        run += w2 < warp ? s_wsum2[w2] : 0;
+                        all += s_wsum2[w2];
+                    }
+                    run += incl - local;
+#pragma unroll
+                    for (int q = 0; q < kPassCap / kThreads; ++q) {
+                        const int k = tid * (kPassCap / kThreads) + q;
+                        s_passp[k] = k < n_pass ? run : INT_MAX;
+                        run += cnt[q];
+                    }
+                    if (tid == 0)
+                        s_passp[kPassCap] = all;
+                }
+                __syncthreads();
+                // (c) threads over the listed cells' boxes
+                const int n_boxes_listed = s_passp[kPassCap];
+                for (int i = tid; i < n_boxes_listed; i += kThreads) {
+                    // the cell of box i: the last k with s_passp[k] <= i
+                    int k = 0;
+#pragma unroll
+                    for (int step = kPassCap / 2; step > 0; step >>= 1)
+                        if (s_passp[k + step] <= i)
+                            k += step;
+                    add_candidate(world, sm.planes, n_planes, s_passb[k] + (i - s_passp[k]), sm, s_ids, box_cap,
+                                  spill, spill_slot, R);
+                }
+                if (tid == 0)
+                    s_npass = 0;
                 __syncthreads();   // the next rows reuse the span arrays
             }
         }
@@ -1089,7 +1201,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                     const float qu = R.au == 0 ? qx : (R.au == 1 ? qy : zq);
                     const float qn = R.an == 0 ? qx : (R.an == 1 ? qy : zq);
                     const float qw = R.dims == 3 ? (R.aw == 0 ? qx : (R.aw == 1 ? qy : zq)) : 0.f;
-                    active = want_bits || R.sn * (qn - R.p_n) > 0.f;
+                    active = want_bits || facing(R, qn);
                     behind = !active;
                     if (active && bl < nb8) {
                         full = box_blocks_all(R, s_box[2 * bl], s_box[2 * bl + 1], qu, qn, qw);
@@ -1133,7 +1245,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 const float qu = R.au == 0 ? qx : (R.au == 1 ? qy : zq);
                 const float qn = R.an == 0 ? qx : (R.an == 1 ? qy : zq);
                 const float qw = R.dims == 3 ? (R.aw == 0 ? qx : (R.aw == 1 ? qy : zq)) : 0.f;
-                const bool front = R.sn * (qn - R.p_n) > 0.f;
+                const bool front = facing(R, qn);
                 if (n_smem > 8) {
                     const int nb_short = min(n_smem, 32);
                     if (lane < nb_short)
@@ -1155,7 +1267,13 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 Plane *pyr = s_pyr[warp];
                 const int npyr = count > kPyramidMinCount ? pyramid_planes(R, qu, qn, qw, pyr) : 0;
                 float v;
-                switch (R.k_rows) {
+                if (EXTRA && (R.cone || (R.flags & VCM_TWO_SIDED))) {
+                    // sides and cone: one sweep variant of their own (8 rows
+                    // per pass, either sign of the row offsets; the host sets
+                    // k_rows = 8 for these requests)
+                    v = sweep_viewpoint<8, true, true>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp,
+                                                       pyr, npyr, tests, rechecks);
+                } else switch (R.k_rows) {
                 case 1: v = sweep_k<1>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
                 case 2: v = sweep_k<2>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
                 case 4: v = sweep_k<4>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
@@ -1198,19 +1316,165 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         atomicExch(&spill_busy[spill_slot], 0);
 }
 
-// Clear the occlusion-bit buffers of the requests that asked for bits
-// (bits are set with atomicOr by the tile kernel).
-__global__ void k_zero_bits(const DevRequest *__restrict__ reqs, int n_req)
+// Launch prologue, in one kernel: the tile queue's counter, every request's
+// counters and, for the requests that asked for bits, their occlusion-bit
+// buffers (the tile kernel sets bits with atomicOr).
+__global__ void k_prologue(const DevRequest *__restrict__ reqs, int n_req, int *__restrict__ work)
 {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nt = (long long)gridDim.x * blockDim.x;
+    if (t == 0)
+        *work = 0;
+    constexpr int kStatWords = (int)(sizeof(vcm_stats) / sizeof(unsigned));
+    for (long long i = t; i < (long long)n_req * kStatWords; i += nt)
+        reinterpret_cast<unsigned *>(reqs[i / kStatWords].stats)[i % kStatWords] = 0u;
     for (int r = 0; r < n_req; ++r) {
         const DevRequest &R = reqs[r];
         if (!(R.flags & VCM_EMIT_BITS) || !R.bits_out)
             continue;
         const long long n = (long long)R.nx * R.ny * R.nl * R.words;
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-             i += (long long)gridDim.x * blockDim.x)
+        for (long long i = t; i < n; i += nt)
             R.bits_out[i] = 0u;
     }
+}
+
+// ---------------------------------------------------------------------------
+// recoloring from stored occlusion bits (incremental gaze change)
+// ---------------------------------------------------------------------------
+
+// Values of one target-centric request from occlusion bits made earlier
+// (R.bits_out is read, not written): no occlusion test, only the sides, the
+// field-of-view cone, strictness and the measure.  Two passes, because the
+// viewpoints that need a measure cluster in the grid:
+//  1. one viewpoint per thread: the side test and the viewpoint's bit words
+//     (fully blocked, or in strict mode any patch blocked, gives v = 0);
+//     the others are appended to a list;
+//  2. one warp per listed viewpoint, lanes over patches, the warp holding
+//     the bit words in registers.  The summation follows the tile kernel's:
+//     a compensated sum per lane, then a fixed-order butterfly.
+
+__device__ __forceinline__ void recolor_point(const DevRequest &R, long long vp, float &qu, float &qn, float &qw)
+{
+    const long long nxy = (long long)R.nx * R.ny;
+    const int layer = (int)(vp / nxy);
+    const long long rem = vp - (long long)layer * nxy;   // nx * ny can pass 2^31
+    const int iy = (int)(rem / R.nx), ix = (int)(rem - (long long)iy * R.nx);
+    const float qx = R.x_coord[ix], qy = R.y_coord[iy], qz = R.dims == 3 ? R.z_coord[layer] : 0.f;
+    qu = R.au == 0 ? qx : (R.au == 1 ? qy : qz);
+    qn = R.an == 0 ? qx : (R.an == 1 ? qy : qz);
+    qw = R.dims == 3 ? (R.aw == 0 ? qx : (R.aw == 1 ? qy : qz)) : 0.f;
+}
+
+__global__ void __launch_bounds__(256) k_recolor_scan(const DevRequest *__restrict__ reqs, int *__restrict__ list,
+                                                      int *__restrict__ n_list)
+{
+    __shared__ DevRequest s_r;
+    if (threadIdx.x == 0)
+        s_r = reqs[0];
+    __syncthreads();
+    const DevRequest &R = s_r;
+    const int lane = threadIdx.x & 31;
+    const long long n = (long long)R.nx * R.ny * R.nl;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    const bool strict = (R.flags & VCM_STRICT) != 0;
+    const unsigned last_mask = (R.P & 31) ? ((1u << (R.P & 31)) - 1u) : 0xffffffffu;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += step) {
+        const long long vp = base + lane;
+        bool live = false;
+        if (vp < n) {
+            float qu, qn, qw;
+            recolor_point(R, vp, qu, qn, qw);
+            if (facing(R, qn)) {
+                const uint32_t *words = R.bits_out + vp * R.words;
+                bool all_blocked = true, any_blocked = false;
+                for (int wd = 0; wd < R.words; ++wd) {
+                    const unsigned full = wd == R.words - 1 ? last_mask : 0xffffffffu;
+                    const unsigned w = __ldg(&words[wd]) & full;
+                    all_blocked &= w == full;
+                    any_blocked |= w != 0u;
+                }
+                live = !all_blocked && !(strict && any_blocked);
+            }
+            if (!live)
+                R.v_out[vp] = 0.f;
+        }
+        const unsigned m = __ballot_sync(kFull, live);
+        int at = 0;
+        if (lane == 0 && m)
+            at = atomicAdd(n_list, __popc(m));
+        at = __shfl_sync(kFull, at, 0);
+        if (live)
+            list[at + __popc(m & ((1u << lane) - 1u))] = (int)vp;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_recolor_measure(const DevRequest *__restrict__ reqs,
+                                                         const int *__restrict__ list, const int *__restrict__ n_list)
+{
+    __shared__ DevRequest s_r;
+    if (threadIdx.x == 0)
+        s_r = reqs[0];
+    __syncthreads();
+    const DevRequest &R = s_r;
+    const int lane = threadIdx.x & 31;
+    const int n = *n_list;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int du = 32 % R.nu, dw = 32 / R.nu;
+    float vmax = 0.f;
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const long long vq = list[i];
+        float qu, qn, qw;
+        recolor_point(R, vq, qu, qn, qw);
+        const uint32_t *words = R.bits_out + vq * R.words;
+        const float rn = qn - R.p_n;
+        const float m_s = R.measure * ((R.flags & VCM_TWO_SIDED) ? fabsf(rn) : R.sn * rn);
+        float sum = 0.f, comp = 0.f;
+        int iu = lane % R.nu, iw = lane / R.nu;
+        unsigned held = 0u;   // bit words k*32 .. k*32+31 of this viewpoint, one per lane
+        for (int j = lane, k = 0; k * 32 < R.P; j += 32, ++k) {
+            if ((k & 31) == 0) {
+                const int wd = k + lane;
+                held = wd < R.words ? __ldg(&words[wd]) : 0u;
+            }
+            const unsigned w = __shfl_sync(kFull, held, k & 31);
+            if (j < R.P) {
+                const bool blocked = (w >> lane) & 1u;
+                const float ru = qu - __ldg(&R.u_coord[iu]), rw = qw - __ldg(&R.w_coord[iw]);
+                if (!blocked && !(R.cone && !in_cone_inline(R, ru, rn, rw))) {
+                    const float d2 = fmaf(rw, rw, fmaf(ru, ru, rn * rn));
+                    float term;
+                    if (R.dims == 3) {
+                        const float ir = rsqrtf(d2);
+                        term = m_s * (ir * ir * ir);
+                    } else {
+                        term = m_s / d2;
+                    }
+                    const float tsum = sum + term;
+                    if (fabsf(sum) >= fabsf(term))
+                        comp += (sum - tsum) + term;
+                    else
+                        comp += (term - tsum) + sum;
+                    sum = tsum;
+                }
+            }
+            // the lane's next patch: 32 further in row-major order
+            iu += du;
+            iw += dw;
+            if (iu >= R.nu) {
+                iu -= R.nu;
+                ++iw;
+            }
+        }
+        float v = sum + comp;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            v += __shfl_xor_sync(kFull, v, off);
+        if (lane == 0)
+            R.v_out[vq] = v;
+        vmax = fmaxf(vmax, v);
+    }
+    if (lane == 0 && vmax > 0.f)
+        atomicMax(&R.stats->vmax_bits, __float_as_uint(vmax));
 }
 
 // ---------------------------------------------------------------------------
@@ -1280,7 +1544,10 @@ cudaError_t init_device()
             }
     if ((e = cudaMemcpyToSymbol(c_tri, tri, sizeof(tri))) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tiles_smem_bytes(kMaxBoxCap))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)tiles_smem_bytes(kMaxBoxCap))) != cudaSuccess)
         return e;
     if (dev >= 0 && dev < 64)
@@ -1347,11 +1614,11 @@ cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, 
     return cudaGetLastError();
 }
 
-int tiles_blocks_per_sm(int box_cap, int k_rows_max)
+int tiles_blocks_per_sm(int box_cap)
 {
-    (void)k_rows_max;
+    // both instantiations have the same launch bounds (4 blocks of kThreads)
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tiles, kThreads, tiles_smem_bytes(box_cap)) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tiles<false>, kThreads, tiles_smem_bytes(box_cap)) !=
         cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
@@ -1359,9 +1626,8 @@ int tiles_blocks_per_sm(int box_cap, int k_rows_max)
 
 cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
                          int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
-                         int box_cap, int k_rows_max, cudaStream_t stream, bool one_tile, int *d_spill_busy)
+                         int box_cap, bool extra, cudaStream_t stream, bool one_tile, int *d_spill_busy)
 {
-    (void)k_rows_max;
     if (total_tiles <= 0)
         return cudaSuccess;
     if (box_cap < 1 || box_cap > kMaxBoxCap)
@@ -1373,17 +1639,24 @@ cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int
             return cudaErrorInvalidValue;
         grid_blocks = total_tiles;
     }
-    k_tiles<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles,
-                                                     d_work, d_spill, box_cap, one_tile ? 1 : 0,
-                                                     d_spill_busy, slots);
+    if (extra)
+        k_tiles<true><<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles,
+                                                               d_work, d_spill, box_cap, one_tile ? 1 : 0,
+                                                               d_spill_busy, slots);
+    else
+        k_tiles<false><<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles,
+                                                                d_work, d_spill, box_cap, one_tile ? 1 : 0,
+                                                                d_spill_busy, slots);
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_bits(const DevRequest *d_reqs, int n_req, cudaStream_t stream)
+cudaError_t launch_prologue(const DevRequest *d_reqs, int n_req, int *d_work, bool any_bits, cudaStream_t stream)
 {
     if (n_req <= 0)
         return cudaSuccess;
-    k_zero_bits<<<152 * 4, 256, 0, stream>>>(d_reqs, n_req);
+    // without bits there are only n_req counters to clear
+    const int blocks = any_bits ? 152 * 4 : std::max(1, std::min(152, (n_req * 16 + 255) / 256));
+    k_prologue<<<blocks, 256, 0, stream>>>(d_reqs, n_req, d_work);
     return cudaGetLastError();
 }
 
@@ -1396,6 +1669,25 @@ cudaError_t launch_quantise(const DevRequest *d_reqs, const long long *d_vp_pref
     if (blocks > 152 * 16)
         blocks = 152 * 16;
     k_quantise<<<(int)blocks, 256, 0, stream>>>(d_reqs, d_vp_prefix, n_req, total_vp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recolor(const DevRequest *d_req, long long n_vp, int sm_count, int *d_list, int *d_n_list,
+                           cudaStream_t stream)
+{
+    if (n_vp <= 0)
+        return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(d_n_list, 0, sizeof(int), stream);
+    if (e != cudaSuccess)
+        return e;
+    long long blocks = (n_vp + 255) / 256;
+    const long long cap = (long long)std::max(sm_count, 1) * 8;
+    if (blocks > cap)
+        blocks = cap;
+    k_recolor_scan<<<(int)blocks, 256, 0, stream>>>(d_req, d_list, d_n_list);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    k_recolor_measure<<<(int)cap, 256, 0, stream>>>(d_req, d_list, d_n_list);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libvcm.so")
 VCM_OK, VCM_PENDING = 0, 1
 VCM_E_ARG, VCM_E_IO, VCM_E_NOMEM, VCM_E_CUDA = -1, -2, -3, -4
 VCM_E_TIMEOUT, VCM_E_CANCELLED, VCM_E_STATE = -5, -6, -7
-VCM_EMIT_BITS, VCM_STRICT, VCM_VIEWER = 1, 2, 4
+VCM_EMIT_BITS, VCM_STRICT, VCM_VIEWER, VCM_TWO_SIDED = 1, 2, 4, 8
 STATUS_NAMES = {0: "VCM_OK", 1: "VCM_PENDING", -1: "VCM_E_ARG", -2: "VCM_E_IO", -3: "VCM_E_NOMEM",
                 -4: "VCM_E_CUDA", -5: "VCM_E_TIMEOUT", -6: "VCM_E_CANCELLED", -7: "VCM_E_STATE"}
 UNITS_PER_M = 1024
@@ -27,7 +27,8 @@ UNITS_PER_M = 1024
 EXPORTS = ["vcm_ctx_create", "vcm_ctx_destroy", "vcm_last_error", "vcm_scene_load_mem", "vcm_scene_load",
            "vcm_scene_save", "vcm_build", "vcm_compute", "vcm_submit", "vcm_submit_batch", "vcm_poll",
            "vcm_result_get", "vcm_result_release", "vcm_cancel", "vcm_set_slots", "vcm_compute_batch",
-           "vcm_autotune", "vcm_set_tune", "vcm_get_tune", "vcm_set_timing_events", "vcm_compute_static"]
+           "vcm_autotune", "vcm_set_tune", "vcm_get_tune", "vcm_set_timing_events", "vcm_compute_static",
+           "vcm_recolor"]
 
 
 class VcmError(RuntimeError):
@@ -43,7 +44,8 @@ class vcm_request(ctypes.Structure):
                 ("grid_origin", ctypes.c_float * 2), ("grid_step", ctypes.c_float * 2),
                 ("grid_nx", ctypes.c_uint32), ("grid_ny", ctypes.c_uint32), ("n_layers", ctypes.c_uint32),
                 ("layer_z", ctypes.POINTER(ctypes.c_float)), ("color_levels", ctypes.c_uint32),
-                ("v_ref", ctypes.c_float), ("flags", ctypes.c_uint32)]
+                ("v_ref", ctypes.c_float), ("flags", ctypes.c_uint32), ("fov_deg", ctypes.c_float),
+                ("gaze", ctypes.c_float * 3)]
 
 
 class vcm_stats(ctypes.Structure):
@@ -89,6 +91,7 @@ def lib():
         L.vcm_scene_save.argtypes = [VP, ctypes.c_char_p]
         L.vcm_build.argtypes = [VP, ctypes.c_float]
         L.vcm_compute.argtypes = [VP, P(vcm_request), VP, VP, VP, VP, VP]
+        L.vcm_recolor.argtypes = [VP, P(vcm_request), VP, VP, VP, VP, VP]
         L.vcm_compute_batch.argtypes = [VP, P(vcm_request), ctypes.c_uint32, P(VP), P(VP), P(VP), VP, VP]
         L.vcm_submit.argtypes = [VP, P(vcm_request), P(ctypes.c_uint64)]
         L.vcm_submit_batch.argtypes = [VP, P(vcm_request), ctypes.c_uint32, P(ctypes.c_uint64)]
@@ -137,6 +140,10 @@ def make_request(d):
     r.color_levels = d["color_levels"]
     r.v_ref = d.get("v_ref", 0.0)
     r.flags = d.get("flags", 0)
+    r.fov_deg = d.get("fov_deg", 0.0)
+    g = d.get("gaze", (0.0, 0.0, 0.0))
+    for k in range(3):
+        r.gaze[k] = g[k]
     return r, z
 
 
@@ -240,6 +247,27 @@ class Context:
         self.vcm_compute(req, v.data_ptr(), c.data_ptr(), b.data_ptr() if b is not None else None,
                          s.data_ptr(), stream.cuda_stream)
         return v, c, b, s
+
+    def vcm_recolor(self, req, d_bits, d_v, d_color, d_stats, stream):
+        r, keep = make_request(req)
+        st = self.L.vcm_recolor(self.h, ctypes.byref(r), d_bits, d_v, d_color, d_stats, stream)
+        return self._ck(st)
+
+    def recolor(self, req, bits, stream=None):
+        """Values and colors of `req` from occlusion bits made earlier (a
+        device tensor from compute(..., emit_bits=True) of the same target
+        and grid), on the current torch stream.  Returns (v, color, stats)."""
+        import torch
+
+        dev = torch.device("cuda", self.device)
+        n = n_viewpoints(req)
+        v = torch.empty(n, dtype=torch.float32, device=dev)
+        c = torch.empty(n, dtype=torch.uint8, device=dev)
+        s = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.vcm_recolor(req, bits.data_ptr(), v.data_ptr(), c.data_ptr(), s.data_ptr(), stream.cuda_stream)
+        return v, c, s
 
     # asynchronous requests ---------------------------------------------------
     def vcm_submit(self, req):

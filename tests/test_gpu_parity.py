@@ -307,7 +307,7 @@ def test_argument_errors(ctx):
     ctx.compute(dict(req, center=[1, 0, 0]))     # one lattice unit off centre is fine
     for r, st in [(dict(req, dims=4), -1), (dict(req, normal=0), -1), (dict(req, color_levels=1), -1),
                   (dict(req, grid_step=[0, 8000]), -1), (dict(req, patches_u=0), -1),
-                  (dict(req, flags=8), -1)]:
+                  (dict(req, flags=16), -1)]:
         with pytest.raises(VcmError) as e:
             ctx.compute(r)
         assert e.value.status == st
@@ -509,3 +509,120 @@ def test_timing_events_bracket_the_tile_kernel(ctx):
         assert a.elapsed_time(b) > 0.0
     finally:
         ctx.vcm_set_timing_events(None, None)
+
+
+# ---------------------------------------------------------------------------
+# two-sided targets and the field-of-view cone
+# ---------------------------------------------------------------------------
+
+def _reduced(which, seed):
+    if which == "2d":
+        return synth.workload_2d(seed=seed)
+    return synth.workload_3d(seed=seed, grid=40, layers=3, patches=(16, 8), n_boxes=300, half_m=400.0,
+                             n_components=5, sigma_m=(60.0, 150.0))
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_two_sided(ctx, which):
+    """Both faces count: viewpoints behind the target get values too, and
+    those in front keep their one-sided values."""
+    from paper_1310_7297_gb300 import VCM_STRICT, VCM_TWO_SIDED
+
+    sc, req = _reduced(which, 51)
+    load(ctx, sc)
+    r = dict(req, flags=VCM_TWO_SIDED)
+    gv, gb, st, err, mism = full_parity(ctx, sc, r)
+    one, _, _, _ = gpu_run(ctx, req, bits=False)
+    behind = (one == 0) & (gv > 0)
+    assert behind.sum() > 50
+    front = one > 0
+    assert np.allclose(gv[front], one[front], rtol=1e-6, atol=0)
+    full_parity(ctx, sc, dict(req, flags=VCM_TWO_SIDED | VCM_STRICT))
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+@pytest.mark.parametrize("case", ["fov120", "fov100_gaze", "two_sided_fov150", "strict_fov130", "fov300"])
+def test_field_of_view(ctx, which, case):
+    """A cone around the gaze axis masks patches; the decision is the same
+    float32 computation on both sides, so values, bits and colors match."""
+    from paper_1310_7297_gb300 import VCM_STRICT, VCM_TWO_SIDED
+
+    sc, req = _reduced(which, 52)
+    load(ctx, sc)
+    r = dict(req)
+    if case == "fov120":
+        r.update(fov_deg=120.0)
+    elif case == "fov100_gaze":
+        r.update(fov_deg=100.0, gaze=[-0.6, 1.0, -0.1])
+    elif case == "two_sided_fov150":
+        r.update(fov_deg=150.0, gaze=[-0.2, 1.0, 0.1], flags=VCM_TWO_SIDED)
+    elif case == "strict_fov130":
+        r.update(fov_deg=130.0, flags=VCM_STRICT)
+    else:
+        r.update(fov_deg=300.0, gaze=[0.0, -1.0, 0.0], flags=VCM_TWO_SIDED)
+    gv, gb, st, err, mism = full_parity(ctx, sc, r)
+    full = O.run(sc, dict(req, flags=r.get("flags", 0)))
+    assert (gv > 0).sum() > 20
+    if case != "fov300":
+        assert (gv < full * (1 - 1e-6)).sum() > 20   # the cone takes some patches away
+
+
+def test_two_sided_and_fov_argument_errors(ctx):
+    from paper_1310_7297_gb300 import VCM_TWO_SIDED, VCM_VIEWER, VcmError
+    from synth import make_request
+
+    sc, req = _reduced("2d", 53)
+    load(ctx, sc)
+    bad = [dict(req, fov_deg=-1.0), dict(req, fov_deg=float("nan")), dict(req, fov_deg=90.0, gaze=[float("inf"), 0, 0])]
+    viewer = make_request(2, (37.0, -12.5), 0, 2, 2.0, 1, (-500.0, -500.0), (10.0, 10.0), (8, 8),
+                          color_levels=8, flags=VCM_VIEWER)
+    bad += [dict(viewer, flags=VCM_VIEWER | VCM_TWO_SIDED), dict(viewer, fov_deg=100.0)]
+    for r in bad:
+        with pytest.raises(VcmError) as e:
+            gpu_run(ctx, r, bits=False)
+        assert "VCM_E_ARG" in str(e.value)
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_recolor_from_bits_for_new_gazes(ctx, which):
+    """One computation with bits, then new fields of view, gazes, sides and
+    strictness from those bits alone: each equals the oracle for that
+    request and the direct computation of it."""
+    import torch
+
+    from paper_1310_7297_gb300 import VCM_STRICT, VCM_TWO_SIDED
+
+    sc, req = _reduced(which, 54)
+    load(ctx, sc)
+    _, _, bits, _ = ctx.compute(req, emit_bits=True)
+    cases = [dict(), dict(fov_deg=120.0), dict(fov_deg=100.0, gaze=[-0.6, 1.0, -0.1]),
+             dict(fov_deg=150.0, gaze=[-0.2, 1.0, 0.1], flags=VCM_TWO_SIDED), dict(fov_deg=90.0, flags=VCM_STRICT),
+             dict(flags=VCM_TWO_SIDED | VCM_STRICT), dict(fov_deg=200.0, color_levels=5, v_ref=0.5)]
+    for extra in cases:
+        r = dict(req, **extra)
+        v, c, s = ctx.recolor(r, bits)
+        torch.cuda.synchronize()
+        gv = v.cpu().numpy().astype(np.float64)
+        ov = O.run(sc, r)
+        compare_v(ov, gv, str(extra))
+        compare_colors(ov, c.cpu().numpy(), r["color_levels"], r.get("v_ref", 0.0))
+        dv, _, _, _ = gpu_run(ctx, r, bits=False)
+        assert np.allclose(gv, dv, rtol=2e-6, atol=0), extra
+        assert (gv > 0).sum() > 20
+
+
+def test_recolor_argument_errors(ctx):
+    from paper_1310_7297_gb300 import VCM_VIEWER, VcmError
+    from synth import make_request
+
+    sc, req = _reduced("2d", 55)
+    load(ctx, sc)
+    _, _, bits, _ = ctx.compute(req, emit_bits=True)
+    viewer = make_request(2, (37.0, -12.5), 0, 2, 2.0, 1, (-500.0, -500.0), (10.0, 10.0), (8, 8),
+                          color_levels=8, flags=VCM_VIEWER)
+    with pytest.raises(VcmError, match="VCM_E_ARG"):
+        ctx.recolor(viewer, bits)
+    with pytest.raises(VcmError, match="VCM_E_ARG"):
+        ctx.vcm_recolor(req, None, 1, None, 1, None)
+    with pytest.raises(VcmError, match="VCM_E_ARG"):
+        ctx.recolor(dict(req, fov_deg=-5.0), bits)
