@@ -511,7 +511,11 @@ __device__ __noinline__ bool in_cone(const DevRequest &R, float ru, float rn, fl
     return in_cone_inline(R, ru, rn, rw);
 }
 
-template <int K, bool MIXED, bool EXTRA>
+// One variant for either sign of the row offsets w - q_w (a per-row sign
+// mask): a viewpoint layer inside the target's height range and one outside
+// it then run the same code, which halves the sweep's hot instruction
+// footprint (a split by sign made the 3D workload 10 % slower).
+template <int K, bool EXTRA>
 __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const float4 *__restrict__ sbox,
                                                  int n_smem, const int *__restrict__ spill, int count,
                                                  const float4 *__restrict__ gbox, float qu, float qn,
@@ -525,7 +529,6 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
     const float dn = R.p_n - qn;
     const float inv_n = rcp_approx(dn);
     const bool sgn_n = dn >= 0.f;
-    const bool sgn_w_uni = qw <= R.w_min;    // all rows at dw >= 0 (used when !MIXED)
     const bool want_bits = (R.flags & VCM_EMIT_BITS) && R.bits_out;
     // strict: any blocked patch zeroes the viewpoint, so the first one ends it
     const bool strict = (R.flags & VCM_STRICT) != 0;
@@ -613,19 +616,11 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                     continue;
                 ++nb;   // boxes whose rows are tested
                 const float a_w = lo.z - qw, b_w = hi.z - qw;
-                const float near_w = sgn_w_uni ? a_w : b_w;
-                const float far_w = sgn_w_uni ? b_w : a_w;
 #pragma unroll
                 for (int m = 0; m < K; ++m) {
-                    float tnw, tfw;
-                    if (MIXED) {
-                        const bool sp = (sgnw >> m) & 1u;
-                        tnw = (sp ? a_w : b_w) * inv_w[m];
-                        tfw = (sp ? b_w : a_w) * inv_w[m];
-                    } else {
-                        tnw = near_w * inv_w[m];
-                        tfw = far_w * inv_w[m];
-                    }
+                    const bool sp = (sgnw >> m) & 1u;
+                    const float tnw = (sp ? a_w : b_w) * inv_w[m];
+                    const float tfw = (sp ? b_w : a_w) * inv_w[m];
                     const float enter = fmaxf(fmaxf(pre_e, tnw), clampv[m]);
                     const float exit_ = fminf(pre_x, tfw);
                     const float mv = exit_ - enter;
@@ -744,19 +739,6 @@ __device__ __forceinline__ float viewer_cell(const DevRequest &R, const float4 *
     return 4.f * asinf(S * S / fmaf(4.f * D, D, S * S));
 }
 
-template <int K>
-__device__ __forceinline__ float sweep_k(const DevRequest &R, const float4 *sbox, int n_smem,
-                                         const int *spill, int count, const float4 *gbox, float qu,
-                                         float qn, float qw, bool front, long long vp, const Plane *pyr,
-                                         int npyr, unsigned long long &tests, unsigned &rechecks)
-{
-    const bool mixed = !(qw <= R.w_min) && !(qw > R.w_max);
-    if (mixed)
-        return sweep_viewpoint<K, true, false>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr,
-                                               npyr, tests, rechecks);
-    return sweep_viewpoint<K, false, false>(R, sbox, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr,
-                                            npyr, tests, rechecks);
-}
 
 // Cull one box against the hull planes and, if it may matter, add it to the
 // tile's candidate list (shared memory, then the block's spill region).
@@ -1269,15 +1251,14 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 float v;
                 if (EXTRA && (R.cone || (R.flags & VCM_TWO_SIDED))) {
                     // sides and cone: one sweep variant of their own (8 rows
-                    // per pass, either sign of the row offsets; the host sets
-                    // k_rows = 8 for these requests)
-                    v = sweep_viewpoint<8, true, true>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp,
-                                                       pyr, npyr, tests, rechecks);
+                    // per pass; the host sets k_rows = 8 for these requests)
+                    v = sweep_viewpoint<8, true>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr,
+                                                 npyr, tests, rechecks);
                 } else switch (R.k_rows) {
-                case 1: v = sweep_k<1>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
-                case 2: v = sweep_k<2>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
-                case 4: v = sweep_k<4>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
-                default: v = sweep_k<8>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+                case 1: v = sweep_viewpoint<1, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+                case 2: v = sweep_viewpoint<2, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+                case 4: v = sweep_viewpoint<4, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+                default: v = sweep_viewpoint<8, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
                 }
                 if (!front)
                     v = 0.f;

@@ -70,6 +70,30 @@ def test_grid_cell_sizes_walk_every_occluder(ctx, cell):
     full_parity(ctx, sc2, req2)
 
 
+def test_dense_cells_overflow_the_walk_list(ctx):
+    """4,000 boxes of 1-3 m over 120 m with a 1.5 m grid: nearly every cell
+    under a tile's footprint holds boxes, so a walk round lists more cells
+    than its list holds and the rest take the per-cell path."""
+    from synth import make_request
+
+    rng = np.random.default_rng(61)
+    n = 4000
+    c = rng.integers(-60 * U, 60 * U, size=(n, 3))
+    c[:, 2] = 0
+    keep = ~((np.abs(c[:, 0]) < 8 * U) & (np.abs(c[:, 1]) < 4 * U))   # off the target
+    c = c[keep]
+    size = rng.integers(1 * U, 3 * U, size=c.shape)
+    lo = c.copy()
+    hi = c + size
+    hi[:, 2] = rng.integers(1 * U, 9 * U, size=c.shape[0])
+    sc = scene(3, list(zip(lo.tolist(), hi.tolist())))
+    req = make_request(3, (0.0, 0.0, 6.0), 0, 2, 8.0, 8, (-60.0, -60.0), (5.0, 5.0), (24, 24),
+                       layers_m=(1.0, 12.0), axis_w=4, height_m=4.0, patches_w=4, color_levels=8)
+    load(ctx, sc, 1.5)
+    gv, gb, st, err, mism = full_parity(ctx, sc, req)
+    assert (gv > 0).sum() > 20 and gb.any()
+
+
 def test_workload_3d_full_size_sampled(ctx):
     """512 x 512 x 5 viewpoints, 5,000 boxes, 32 x 16 patches, in the launch
     configuration the benchmark times; the oracle checks 1,200 viewpoints."""
