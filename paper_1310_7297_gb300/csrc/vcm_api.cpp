@@ -1916,12 +1916,18 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
             cs[i].flags = 0;
             max_vp = std::max<size_t>(max_vp, (size_t)cs[i].n_vp);
         }
+        // Shapes are compared at saturation, as a batch runs: a class's
+        // samples are replicated in one launch until it holds several waves
+        // of tiles, and a shape scores the time per copy of the samples.
+        // (Timing a small request alone measures latency on an idle GPU and
+        // favours small tiles, which only add per-tile work in a batch.)
+        constexpr size_t kMaxCopies = 4096;
         float *d_v = nullptr;
         vcm_stats *d_stats = nullptr;
         cudaStream_t s = nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         CUDA_TRY(cudaMalloc(&d_v, max_vp * sizeof(float)));
-        CUDA_TRY(cudaMalloc(&d_stats, sizeof(vcm_stats)));
+        CUDA_TRY(cudaMalloc(&d_stats, kMaxCopies * sizeof(vcm_stats)));
         CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
         CUDA_TRY(cudaEventCreate(&e0));
         CUDA_TRY(cudaEventCreate(&e1));
@@ -1932,31 +1938,49 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
         vcm_tune best[kTuneClasses];
         bool seen[kTuneClasses] = {false};
         std::lock_guard<std::mutex> g(ctx->mu);
-        // Time one shape on a class's samples: best of three launches each,
-        // summed over the samples (one warm-up launch first).
-        auto time_shape = [&](const std::vector<const Canon *> &mine, const vcm_tune &t, double &total) -> vcm_status {
-            total = 0.0;
-            for (const Canon *c : mine) {
-                std::vector<const Canon *> one{c};
-                std::vector<vcm_tune> sh{t};
-                float *vv[1] = {d_v};
-                vcm_status st2 = enqueue_launch(ctx, ctx->direct, one, sh, vv, nullptr, nullptr, d_stats, s);
-                if (st2 != VCM_OK)
-                    return st2;
-                float best_one = 1e30f;
-                for (int rep = 0; rep < 3; ++rep) {
-                    CUDA_TRY(cudaEventRecord(e0, s));
-                    if ((st2 = enqueue_launch(ctx, ctx->direct, one, sh, vv, nullptr, nullptr, d_stats, s)) != VCM_OK)
-                        return st2;
-                    CUDA_TRY(cudaEventRecord(e1, s));
-                    CUDA_TRY(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-                    best_one = std::min(best_one, ms);
+        // Time requests with their shapes, replicated to saturation; the
+        // score is the time per copy of the set.
+        auto time_set = [&](const std::vector<const Canon *> &mine, const std::vector<vcm_tune> &ts,
+                            double &per_copy) -> vcm_status {
+            uint32_t cap = 32;
+            for (const vcm_tune &t : ts)
+                cap = std::max(cap, t.box_cap);
+            const long long want = 4LL * tiles_blocks_per_sm((int)cap) * ctx->sm_count;
+            std::vector<const Canon *> batch;
+            std::vector<vcm_tune> sh;
+            long long n_tiles = 0;
+            int copies = 0;
+            while ((n_tiles < want || copies == 0) && batch.size() + mine.size() <= kMaxCopies) {
+                for (size_t i = 0; i < mine.size(); ++i) {
+                    batch.push_back(mine[i]);
+                    sh.push_back(ts[i]);
+                    DevRequest d{};
+                    fill_shape(*mine[i], ts[i], d);
+                    n_tiles += d.n_tiles;
                 }
-                total += best_one;
+                ++copies;
             }
+            std::vector<float *> vv(batch.size(), d_v);   // the copies share one output (timing only)
+            vcm_status st2 = enqueue_launch(ctx, ctx->direct, batch, sh, vv.data(), nullptr, nullptr, d_stats, s);
+            if (st2 != VCM_OK)
+                return st2;
+            float best_one = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                CUDA_TRY(cudaEventRecord(e0, s));
+                if ((st2 = enqueue_launch(ctx, ctx->direct, batch, sh, vv.data(), nullptr, nullptr, d_stats, s)) !=
+                    VCM_OK)
+                    return st2;
+                CUDA_TRY(cudaEventRecord(e1, s));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                best_one = std::min(best_one, ms);
+            }
+            per_copy = best_one / copies;
             return VCM_OK;
+        };
+        auto time_shape = [&](const std::vector<const Canon *> &mine, const vcm_tune &t, double &per_copy) {
+            return time_set(mine, std::vector<vcm_tune>(mine.size(), t), per_copy);
         };
         for (int cls = 0; cls < kTuneClasses; ++cls) {
             std::vector<const Canon *> mine;
@@ -1982,6 +2006,26 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
                             best[cls] = t;
                         }
                     }
+        }
+        // The classes run together in a batch: keep the tuned shapes only if
+        // all samples together, each with its class's shape, beat the
+        // default by 3 % as well.
+        {
+            std::vector<const Canon *> all;
+            std::vector<vcm_tune> tuned_sh, default_sh;
+            for (auto &c : cs) {
+                all.push_back(&c);
+                tuned_sh.push_back(best[tune_class(c.P)]);
+                default_sh.push_back(default_tune());
+            }
+            double t_tuned = 0.0, t_default = 0.0;
+            if ((st = time_set(all, default_sh, t_default)) != VCM_OK)
+                return st;
+            if ((st = time_set(all, tuned_sh, t_tuned)) != VCM_OK)
+                return st;
+            if (!(t_tuned < 0.97 * t_default))
+                for (int cls = 0; cls < kTuneClasses; ++cls)
+                    best[cls] = default_tune();
         }
         for (int cls = 0; cls < kTuneClasses; ++cls)
             if (seen[cls])

@@ -13,6 +13,7 @@ namespace vcm {
 constexpr int kWarps = 4;                 // warps per block of the tile kernel
 constexpr int kThreads = kWarps * 32;
 constexpr int kPassCap = 2 * kThreads;       // cells listed per round of the grid walk
+constexpr int kDistClasses = 128;            // distance classes of the candidate counting sort
 constexpr int kMaxPlanes = 32;            // separating planes kept per tile hull
 constexpr float kBand = 1e-6f;            // FP32 slab margin re-decided in FP64
 constexpr int kMaxBoxCap = 5000;          // candidate boxes a tile stages in shared memory

@@ -417,7 +417,8 @@ __device__ __forceinline__ bool one_box_blocks_all(const DevRequest &R, const fl
 // hull, so the half-space holds the whole pyramid whatever the plane's
 // orientation; a degenerate plane only culls less.  Lanes 0..5 each write
 // one plane (NaN-free: degenerate normals are dropped); returns the count.
-__device__ __forceinline__ int pyramid_planes(const DevRequest &R, float qu, float qn, float qw, Plane *out)
+// Not inlined: each sweep variant would carry a copy (1 % on the 3D step).
+__device__ __noinline__ int pyramid_planes(const DevRequest &R, float qu, float qn, float qw, Plane *out)
 {
     const int lane = threadIdx.x & 31;
     // rectangle corners in order (u_min,w_min) (u_max,w_min) (u_max,w_max) (u_min,w_max)
@@ -779,6 +780,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
     __shared__ int s_und[kMaxTileViewpoints];   // viewpoints left by the one-box check
     __shared__ int s_rowpre[kThreads], s_rowx[kThreads], s_wsum[kWarps];   // cell-row spans
     __shared__ int s_passb[kPassCap], s_passn[kPassCap], s_passp[kPassCap + 1], s_wsum2[kWarps], s_npass;
+    __shared__ int s_hist[kDistClasses];   // counting sort of long candidate lists
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     __shared__ int s_spill_slot;
@@ -1105,30 +1107,53 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                         s_ids[lane] = (int)(key & 0xffffffffu);
                 }
             } else {
-                unsigned long long *keyed = reinterpret_cast<unsigned long long *>(s_box);
-                int N = 1;
-                while (N < n_smem)
-                    N <<= 1;
-                for (int i = tid; i < N; i += kThreads)
-                    keyed[i] = i < n_smem ? key_of(i) : ~0ull;
+                // longer lists: a counting sort into distance classes (4 per
+                // doubling of the squared distance, 128 classes from 1 m^2),
+                // near classes first; order within a class is arbitrary.
+                // Results do not depend on the order, only how soon the
+                // sweeps stop; this takes 4 barriers where a bitonic sort of
+                // 256 keys took 36.
+                int *cls_rank = reinterpret_cast<int *>(s_box);   // s_box is free until staging
+                int *placed = cls_rank + n_smem;
+                for (int i = tid; i < kDistClasses; i += kThreads)
+                    s_hist[i] = 0;
                 __syncthreads();
-                for (int k = 2; k <= N; k <<= 1) {
-                    for (int j = k >> 1; j > 0; j >>= 1) {
-                        for (int i = tid; i < N; i += kThreads) {
-                            const int p = i ^ j;
-                            if (p > i) {
-                                const unsigned long long a = keyed[i], b = keyed[p];
-                                if ((a > b) == ((i & k) == 0)) {
-                                    keyed[i] = b;
-                                    keyed[p] = a;
-                                }
-                            }
-                        }
-                        __syncthreads();
+                for (int i = tid; i < n_smem; i += kThreads) {
+                    const unsigned bits = (unsigned)(key_of(i) >> 32);   // float bits of d^2 >= 0
+                    const int c = (int)min((unsigned)(kDistClasses - 1), bits > 0x3f800000u ? (bits - 0x3f800000u) >> 21 : 0u);
+                    cls_rank[i] = (c << 24) | atomicAdd(&s_hist[c], 1);
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    // exclusive scan of the class counts, kDistClasses / 32 per lane
+                    int cnt[kDistClasses / 32], sum = 0;
+#pragma unroll
+                    for (int q = 0; q < kDistClasses / 32; ++q) {
+                        cnt[q] = s_hist[lane * (kDistClasses / 32) + q];
+                        sum += cnt[q];
+                    }
+                    int incl = sum;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int t = __shfl_up_sync(kFull, incl, off);
+                        if (lane >= off)
+                            incl += t;
+                    }
+                    int run = incl - sum;
+#pragma unroll
+                    for (int q = 0; q < kDistClasses / 32; ++q) {
+                        s_hist[lane * (kDistClasses / 32) + q] = run;
+                        run += cnt[q];
                     }
                 }
+                __syncthreads();
+                for (int i = tid; i < n_smem; i += kThreads) {
+                    const int cr = cls_rank[i];
+                    placed[s_hist[cr >> 24] + (cr & 0xffffff)] = s_ids[i];
+                }
+                __syncthreads();
                 for (int i = tid; i < n_smem; i += kThreads)
-                    s_ids[i] = (int)(keyed[i] & 0xffffffffu);
+                    s_ids[i] = placed[i];
             }
             __syncthreads();
         }

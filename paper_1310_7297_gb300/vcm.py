@@ -31,6 +31,14 @@ EXPORTS = ["vcm_ctx_create", "vcm_ctx_destroy", "vcm_last_error", "vcm_scene_loa
            "vcm_recolor"]
 
 
+class _DeviceArray:
+    """A device buffer described by __cuda_array_interface__ (version 3)."""
+
+    def __init__(self, addr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (addr, False),
+                                         "version": 3, "strides": None, "stream": None}
+
+
 class VcmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
@@ -307,6 +315,29 @@ class Context:
         if copy:
             v, c = v.copy(), c.copy()
             b = b.copy() if b is not None else None
+        st = {k: getattr(res.stats, k) for k, _ in vcm_stats._fields_}
+        st["latency_ms"] = res.latency_ms
+        return v, c, b, st
+
+    def vcm_result_device(self, ticket):
+        """Zero-copy torch views (v, color, bits or None, stats dict) of a
+        finished ticket's device buffers, which the context owns: valid until
+        vcm_result_release(ticket).  Exported through
+        __cuda_array_interface__ (no stream: the result is complete)."""
+        import torch
+
+        res = vcm_result()
+        self._ck(self.L.vcm_result_get(self.h, ticket, ctypes.byref(res)))
+        n = res.n_viewpoints
+        dev = torch.device("cuda", self.device)
+
+        def view(addr, shape, typestr):
+            return torch.as_tensor(_DeviceArray(int(addr), shape, typestr), device=dev)
+
+        v = view(res.d_v, (n,), "<f4")
+        c = view(res.d_color, (n,), "|u1")
+        # bit words as int32 (the same 32 bits; torch's uint32 support is partial)
+        b = view(res.d_bits, (n, res.words_per_viewpoint), "<i4") if res.d_bits else None
         st = {k: getattr(res.stats, k) for k, _ in vcm_stats._fields_}
         st["latency_ms"] = res.latency_ms
         return v, c, b, st

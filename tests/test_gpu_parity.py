@@ -307,6 +307,12 @@ def test_submit_poll_matches_direct(ctx):
         assert np.array_equal(v.astype(np.float64), ref[0]) and np.array_equal(c, ref[1])
         assert np.array_equal(b, ref[2])
         assert st["latency_ms"] > 0 and st["segments"] == len(v) * r["patches_u"] * r["patches_w"]
+        # zero-copy device views of the same result
+        dv, dc, db, dst = ctx.vcm_result_device(t)
+        assert dv.is_cuda and dv.dtype.is_floating_point and dc.shape == c.shape
+        assert np.array_equal(dv.cpu().numpy(), v) and np.array_equal(dc.cpu().numpy(), c)
+        assert np.array_equal(db.cpu().numpy().view(np.uint32), b)
+        assert dst["segments"] == st["segments"]
         ctx.vcm_result_release(t)
 
 
