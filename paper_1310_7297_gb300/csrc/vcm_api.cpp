@@ -1933,7 +1933,10 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
         CUDA_TRY(cudaEventCreate(&e1));
         const uint32_t tiles[][2] = {{8, 4}, {8, 8}, {16, 8}, {32, 8}, {16, 16}};
         const uint32_t caps[] = {512, 1024, 2048};
-        const uint32_t ks[] = {2, 4, 8};
+        // Rows per pass stay automatic: a batch whose classes used different
+        // row counts would keep several sweep variants hot at once, a cost
+        // that timing one class at a time does not see (the kernel is
+        // sensitive to its instruction footprint).
         double best_ms[kTuneClasses];
         vcm_tune best[kTuneClasses];
         bool seen[kTuneClasses] = {false};
@@ -1995,17 +1998,16 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
             if ((st = time_shape(mine, best[cls], best_ms[cls])) != VCM_OK)
                 return st;
             for (auto &tl : tiles)
-                for (uint32_t cap : caps)
-                    for (uint32_t k : ks) {
-                        vcm_tune t{tl[0], tl[1], k, cap};
-                        double total = 0.0;
-                        if ((st = time_shape(mine, t, total)) != VCM_OK)
-                            return st;
-                        if (total < 0.97 * best_ms[cls]) {
-                            best_ms[cls] = total;
-                            best[cls] = t;
-                        }
+                for (uint32_t cap : caps) {
+                    vcm_tune t{tl[0], tl[1], default_tune().patch_k, cap};
+                    double total = 0.0;
+                    if ((st = time_shape(mine, t, total)) != VCM_OK)
+                        return st;
+                    if (total < 0.97 * best_ms[cls]) {
+                        best_ms[cls] = total;
+                        best[cls] = t;
                     }
+                }
         }
         // The classes run together in a batch: keep the tuned shapes only if
         // all samples together, each with its class's shape, beat the
