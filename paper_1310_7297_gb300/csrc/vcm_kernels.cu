@@ -549,6 +549,20 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
         const float col_d2 = fmaf(ru, ru, rn * rn);
         // measure x |r| cos(theta); a two-sided target is measured from either side
         const float m_s = R.measure * ((EXTRA && (R.flags & VCM_TWO_SIDED)) ? fabsf(rn) : R.sn * rn);
+        // The measure: a plain sum over each group of up to 8 of the lane's
+        // rows (error <= 7u of the group's total, the terms being >= 0), and a
+        // Neumaier-compensated sum of the group totals, so the bound holds for
+        // any patch count.
+        float psum = 0.f;
+        auto add_group = [&](float &g) {
+            const float tsum = sum + g;
+            if (fabsf(sum) >= fabsf(g))
+                comp += (sum - tsum) + g;
+            else
+                comp += (g - tsum) + sum;
+            sum = tsum;
+            g = 0.f;
+        };
         for (int rp = 0; rp < R.row_passes && !(strict_exit && strict_fail); ++rp) {
             float inv_w[K], clampv[K];
             unsigned valid = 0, sgnw = 0;
@@ -673,17 +687,20 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                         } else {
                             term = m_s / d2;               // len |r| cos(theta) / |r|^2
                         }
-                        // Neumaier compensated accumulation
-                        const float tsum = sum + term;
-                        if (fabsf(sum) >= fabsf(term))
-                            comp += (sum - tsum) + term;
-                        else
-                            comp += (term - tsum) + sum;
-                        sum = tsum;
+                        // an add the compiler cannot fuse with the term's
+                        // product, so every specialised copy of this loop
+                        // rounds the same way
+                        psum = __fadd_rn(psum, term);
                     }
                 }
             }
+            // a group closes after every 8 of the lane's rows (K divides 8, so
+            // the grouping and the result do not depend on K) and at the end
+            // of the column pass
+            if (((rp + 1) * K) % 8 == 0 || rp + 1 == R.row_passes)
+                add_group(psum);
         }
+        add_group(psum);   // what a strict early exit left
     }
     float v = sum + comp;
     // fixed-order butterfly: every lane ends with the same value
