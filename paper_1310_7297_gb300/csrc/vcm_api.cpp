@@ -696,6 +696,7 @@ struct Prepared {
     size_t n = 0;
     bool extra = false;   // a request is two-sided or has a field-of-view cone
     bool any_bits = false;   // a request emits occlusion bits
+    bool tile_check = false;   // every request has many patches: whole-tile check
 };
 
 bool needs_extra(const Canon &c) { return c.cone || (c.flags & VCM_TWO_SIDED); }
@@ -713,9 +714,11 @@ vcm_status prepare_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *
     P.blocks = grid_blocks_for(ctx, P.box_cap, P.L.total_tiles);
     P.n = cs.size();
     P.extra = P.any_bits = false;
+    P.tile_check = !cs.empty();
     for (const Canon *c : cs) {
         P.extra = P.extra || needs_extra(*c);
         P.any_bits = P.any_bits || (c->flags & VCM_EMIT_BITS);
+        P.tile_check = P.tile_check && c->P >= kTileCheckMinPatches;
     }
     vcm_status st = ensure_slot(ctx, s, P.L.bytes, cs.size(), P.blocks, sync_stream);
     if (st != VCM_OK)
@@ -746,7 +749,7 @@ vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *st
     if (timed && ctx->ev_before)
         CUDA_TRY(cudaEventRecord(ctx->ev_before, stream));
     CUDA_TRY(launch_tiles(ctx->scene, d_reqs, d_tiles, (int)P.n, P.L.total_tiles, s.d_work, s.d_spill,
-                          P.blocks, P.box_cap, P.extra, stream, one_tile, s.d_spill_busy));
+                          P.blocks, P.box_cap, P.extra, P.tile_check, stream, one_tile, s.d_spill_busy));
     if (timed && ctx->ev_after)
         CUDA_TRY(cudaEventRecord(ctx->ev_after, stream));
     CUDA_TRY(launch_quantise(d_reqs, d_vps, (int)P.n, P.L.total_vp, stream));
@@ -1878,7 +1881,7 @@ vcm_status vcm_compute_static(const float *lo, const float *hi, uint32_t n_boxes
         const int blocks = std::max(1, std::min(lay.total_tiles, tiles_blocks_per_sm((int)t.box_cap) * sm_count));
         CUDA_TRY(launch_prologue(d_reqs, 1, s_work, (c.flags & VCM_EMIT_BITS) != 0, sm));
         CUDA_TRY(launch_tiles(sc, d_reqs, d_tiles, 1, lay.total_tiles, s_work, s_spill, blocks, (int)t.box_cap,
-                              needs_extra(c), sm));
+                              needs_extra(c), c.P >= kTileCheckMinPatches, sm));
         CUDA_TRY(launch_quantise(d_reqs, d_vps, 1, lay.total_vp, sm));
         return VCM_OK;
     } catch (const std::exception &ex) {

@@ -14,6 +14,7 @@ constexpr int kWarps = 4;                 // warps per block of the tile kernel
 constexpr int kThreads = kWarps * 32;
 constexpr int kPassCap = 2 * kThreads;       // cells listed per round of the grid walk
 constexpr int kDistClasses = 128;            // distance classes of the candidate counting sort
+constexpr int kTileCheckMinPatches = 1024;   // launches whose requests all have this many use the tile check
 constexpr int kMaxPlanes = 32;            // separating planes kept per tile hull
 constexpr float kBand = 1e-6f;            // FP32 slab margin re-decided in FP64
 constexpr int kMaxBoxCap = 5000;          // candidate boxes a tile stages in shared memory
@@ -90,9 +91,11 @@ cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, 
 // grid_blocks * n_boxes ints for candidate lists longer than box_cap.
 // `extra` must be set when any request is two-sided or has a field-of-view
 // cone: it selects the tile kernel's instantiation that handles them.
+// `tile_check` selects the instantiation with the whole-tile check (any
+// launch may use either; it pays when every request has many patches).
 cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
                          int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
-                         int box_cap, bool extra, cudaStream_t stream, bool one_tile = false,
+                         int box_cap, bool extra, bool tile_check, cudaStream_t stream, bool one_tile = false,
                          int *d_spill_busy = nullptr);
 // Colors and edge counts for all viewpoints of n_req requests (grid over the
 // concatenated viewpoints, `d_vp_prefix` = exclusive prefix, n_req + 1).

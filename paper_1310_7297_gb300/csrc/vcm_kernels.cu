@@ -373,6 +373,24 @@ __device__ __forceinline__ bool box_blocks_all(const DevRequest &R, float4 lo, f
            fminf(fminf(fu1, fw1), x0) - fmaxf(fmaxf(nu1, nw1), e0) > kBand;
 }
 
+// True if the box certainly blocks the segments from all four corner
+// viewpoints (x0|x1, y0|y1, layer z) of a tile to the four extreme patch
+// centres (see the whole-tile check in the tile kernel).  Not inlined: it
+// runs once per tile and would add to the tile kernel's registers.
+__device__ __noinline__ bool box_blocks_tile(const DevRequest &R, float4 lo, float4 hi, float x0, float x1, float y0,
+                                             float y1, float z)
+{
+    for (int c = 0; c < 4; ++c) {
+        const float qx = (c & 1) ? x1 : x0, qy = (c & 2) ? y1 : y0;
+        const float qu = R.au == 0 ? qx : (R.au == 1 ? qy : z);
+        const float qn = R.an == 0 ? qx : (R.an == 1 ? qy : z);
+        const float qw = R.dims == 3 ? (R.aw == 0 ? qx : (R.aw == 1 ? qy : z)) : 0.f;
+        if (!box_blocks_all(R, lo, hi, qu, qn, qw))
+            return false;
+    }
+    return true;
+}
+
 // True if one of the first `nb` (<= 32) staged boxes certainly blocks the
 // segments from q to all four extreme patch centres.  On the target plane the
 // points whose segment to q meets a convex box form a convex set (a segment
@@ -782,7 +800,12 @@ __device__ __forceinline__ void add_candidate(const float4 *__restrict__ world, 
 // without spilling, and the fifth block hides more of the dependency and
 // barrier latency that bound it (4 -> 5 blocks: 3D step -5 %, a 256-request
 // batch -11 %; 6 blocks spill and lose on large scenes).
-template <bool EXTRA>
+// TILE_CHECK: the instantiation with the whole-tile check below, for
+// launches whose requests all have many patches (the host picks it).  It
+// decides whole tiles, which pays when a viewpoint's own work is large (the
+// 100,000-box scene with 64 x 32 patches: -10 %); in the other instantiation
+// its code alone cost a few % on smaller requests.
+template <bool EXTRA, bool TILE_CHECK>
 __global__ void __launch_bounds__(kThreads, 5)
 k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict__ tile_prefix,
         int n_req, int total_tiles, int *__restrict__ work, int *__restrict__ spill_all, int box_cap,
@@ -1190,6 +1213,38 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         unsigned long long tests = 0, corner_tests = 0;
         unsigned rechecks = 0, shortcuts = 0;
         float vmax = 0.f;
+
+        // Whole-tile check.  For a fixed patch, the viewpoints whose segment
+        // to it meets a convex box form a convex set (the box's shadow seen
+        // from the patch), so a box that certainly blocks the segments from
+        // the tile's four corner viewpoints to an extreme patch centre blocks
+        // it from the whole tile rectangle; the one-box argument over the
+        // target plane then covers every patch of every viewpoint.  Threads
+        // take the nearest candidates, one each, against all 16 segments.
+        bool tile_blocked = false;
+        if (TILE_CHECK && !viewer) {
+            bool full = false;
+            if (tid < min(n_smem, kThreads)) {
+                full = box_blocks_tile(R, s_box[2 * tid], s_box[2 * tid + 1], R.x_coord[ix0], R.x_coord[ix1 - 1],
+                                       R.y_coord[iy0], R.y_coord[iy1 - 1], zq);
+                corner_tests += 16;
+            }
+            tile_blocked = __syncthreads_or(full) != 0;
+            if (tile_blocked) {
+                for (int i = tid; i < tn; i += kThreads) {
+                    const int ix = ix0 + i % tw, iy = iy0 + i / tw;
+                    const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
+                    R.v_out[vp] = 0.f;
+                    if (want_bits)
+                        for (int wd = 0; wd < R.words; ++wd) {
+                            const int rem = R.P - 32 * wd;
+                            R.bits_out[vp * R.words + wd] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+                        }
+                }
+                if (tid == 0)
+                    shortcuts += (unsigned)tn;
+            }
+        }
         if (viewer) {
             // viewer-centric: threads take cells, one segment each
             for (int vi = tid; vi < tn; vi += kThreads) {
@@ -1209,7 +1264,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // is almost always among them); the viewpoints it leaves open are
         // listed and then taken one per warp for the check over the 32
         // nearest and the separable sweep.
-        for (; !viewer;) {
+        for (; !viewer && !tile_blocked;) {
             int base = 0;
             if (lane == 0)
                 base = atomicAdd(&s_next, 4);
@@ -1257,7 +1312,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         }
         __syncthreads();
         // then the undecided viewpoints, one per warp at a time
-        const int n_und = viewer ? 0 : sm.n_und;
+        const int n_und = (viewer || tile_blocked) ? 0 : sm.n_und;
         for (;;) {
             int k = 0;
             if (lane == 0)
@@ -1571,12 +1626,12 @@ cudaError_t init_device()
             }
     if ((e = cudaMemcpyToSymbol(c_tri, tri, sizeof(tri))) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)tiles_smem_bytes(kMaxBoxCap))) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)tiles_smem_bytes(kMaxBoxCap))) != cudaSuccess)
-        return e;
+    const void *kernels[4] = {(const void *)k_tiles<false, false>, (const void *)k_tiles<true, false>,
+                              (const void *)k_tiles<false, true>, (const void *)k_tiles<true, true>};
+    for (const void *k : kernels)
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)tiles_smem_bytes(kMaxBoxCap))) != cudaSuccess)
+            return e;
     if (dev >= 0 && dev < 64)
         done[dev] = true;
     return cudaSuccess;
@@ -1643,9 +1698,9 @@ cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, 
 
 int tiles_blocks_per_sm(int box_cap)
 {
-    // both instantiations have the same launch bounds (5 blocks of kThreads)
+    // all instantiations have the same launch bounds (5 blocks of kThreads)
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tiles<false>, kThreads, tiles_smem_bytes(box_cap)) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tiles<false, false>, kThreads, tiles_smem_bytes(box_cap)) !=
         cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
@@ -1653,7 +1708,8 @@ int tiles_blocks_per_sm(int box_cap)
 
 cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
                          int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
-                         int box_cap, bool extra, cudaStream_t stream, bool one_tile, int *d_spill_busy)
+                         int box_cap, bool extra, bool tile_check, cudaStream_t stream, bool one_tile,
+                         int *d_spill_busy)
 {
     if (total_tiles <= 0)
         return cudaSuccess;
@@ -1666,14 +1722,10 @@ cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int
             return cudaErrorInvalidValue;
         grid_blocks = total_tiles;
     }
-    if (extra)
-        k_tiles<true><<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles,
-                                                               d_work, d_spill, box_cap, one_tile ? 1 : 0,
-                                                               d_spill_busy, slots);
-    else
-        k_tiles<false><<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles,
-                                                                d_work, d_spill, box_cap, one_tile ? 1 : 0,
-                                                                d_spill_busy, slots);
+    auto kernel = extra ? (tile_check ? k_tiles<true, true> : k_tiles<true, false>)
+                        : (tile_check ? k_tiles<false, true> : k_tiles<false, false>);
+    kernel<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles, d_work, d_spill,
+                                                    box_cap, one_tile ? 1 : 0, d_spill_busy, slots);
     return cudaGetLastError();
 }
 
