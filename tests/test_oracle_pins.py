@@ -12,6 +12,8 @@ Each group targets a plausible mistake:
   * invariants: a full wall gives zero, adding boxes never clears a bit,
     mirror symmetry, viewpoints behind the target or inside a box give zero;
   * colors: the quantiser's defining properties;
+  * blocking is convex in the viewpoint and in the patch (the one-box
+    shortcuts of the GPU path rest on it), by the exact predicate;
   * sides and field of view: mirror images through the target plane and
     through x = 0, a cone equal to a cropped target, the paper's FOV region
     bounded by rays from the target ends.
@@ -635,3 +637,41 @@ def test_fov_with_strict_mode_and_two_sided():
             if ys[iy] == -ys[iy2] and ys[iy] != 0:
                 for ix in range(nx):
                     assert two[iy * nx + ix] == two[iy2 * nx + ix]
+
+
+def test_blocking_is_convex_in_viewpoint_and_in_patch():
+    """The one-box shortcuts rest on two convexity facts, checked here with
+    the exact predicate: for a fixed patch point p, if a box blocks the
+    segments from the four corners of a horizontal rectangle of viewpoints,
+    it blocks those from every point of the rectangle; and for a fixed
+    viewpoint, likewise for the corners of a vertical target rectangle."""
+    rng = np.random.default_rng(31)
+    tried = hit_v = hit_p = 0
+    for _ in range(3000):
+        lo = rng.integers(-40 * U, 30 * U, size=3)
+        lo[2] = 0
+        hi = lo + rng.integers(4 * U, 30 * U, size=3)
+        # viewpoint rectangle (z = const) and a patch point p
+        x0, y0 = rng.integers(-80 * U, 60 * U, size=2)
+        x1, y1 = x0 + int(rng.integers(1, 20 * U)), y0 + int(rng.integers(1, 20 * U))
+        z = int(rng.integers(0, 10 * U))
+        p = [int(rng.integers(-10 * U, 10 * U)), int(rng.integers(40 * U, 60 * U)), int(rng.integers(20 * U, 40 * U))]
+        corners = [[x, y, z] for x in (x0, x1) for y in (y0, y1)]
+        tried += 1
+        if all(O.segment_hits_box(3, q, p, lo, hi) for q in corners):
+            hit_v += 1
+            for _ in range(8):
+                q = [int(rng.integers(x0, x1 + 1)), int(rng.integers(y0, y1 + 1)), z]
+                assert O.segment_hits_box(3, q, p, lo, hi)
+        # target rectangle (y = const) seen from a viewpoint q
+        q = [int(rng.integers(-80 * U, 60 * U)), int(rng.integers(-80 * U, -50 * U)), int(rng.integers(0, 10 * U))]
+        u0, w0 = int(rng.integers(-10 * U, 5 * U)), int(rng.integers(20 * U, 30 * U))
+        u1, w1 = u0 + int(rng.integers(1, 10 * U)), w0 + int(rng.integers(1, 10 * U))
+        yt = int(rng.integers(40 * U, 60 * U))
+        pcs = [[u, yt, w] for u in (u0, u1) for w in (w0, w1)]
+        if all(O.segment_hits_box(3, q, pp, lo, hi) for pp in pcs):
+            hit_p += 1
+            for _ in range(8):
+                pp = [int(rng.integers(u0, u1 + 1)), yt, int(rng.integers(w0, w1 + 1))]
+                assert O.segment_hits_box(3, q, pp, lo, hi)
+    assert hit_v > 30 and hit_p > 30, (hit_v, hit_p)
