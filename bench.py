@@ -729,6 +729,65 @@ def run_gaze(args):
     ctx.close()
 
 
+def run_equivisible(args):
+    """The paper's own equi-visible colouring (distance and angle partition,
+    a colour per cell from its centre; CPU) against the dense GPU map of the
+    same 2D target, by the error of Eq. 6, for the angular resolutions of
+    Table II.  No obstacles: the partition is the paper's step before it
+    accounts for them.  Target: a 10 m segment facing +y; grid: 1024 x 1024
+    cells over 1 km; 16 colour levels, each map normalised by its own
+    maximum; the near point is 1 m."""
+    import torch
+
+    import synth
+    from paper_1310_7297_gb300 import Context
+    from paper_1310_7297_gb300 import build as B
+    from paper_1310_7297_gb300 import equivisible as E
+
+    B.build()
+    S, n, half, levels = 10.0, 1024, 500.0, 16
+    scene = synth.Scene(2, np.zeros((0, 3), np.int64), np.zeros((0, 3), np.int64))
+    req = synth.make_request(2, (0.0, 0.0), synth.AXIS_PX, synth.AXIS_PY, S, 64, (-half, -half),
+                             (2 * half / n, 2 * half / n), (n, n), color_levels=levels)
+    ctx = Context(0)
+    ctx.load_scene(scene)
+    ctx.vcm_build(0.0)
+    t0 = time.perf_counter()
+    v, c, _, _ = ctx.compute(req)
+    torch.cuda.synchronize()
+    gpu_ms = 1e3 * (time.perf_counter() - t0)
+    c_dense = c.cpu().numpy().astype(np.int64)
+    xs = -half + (np.arange(n) + 0.5) * (2 * half / n)
+    X, Y = np.meshgrid(xs, xs)
+    X, Y = X.ravel(), Y.ravel()
+
+    def subtended(D, a_deg):
+        # exact angle subtended by the segment from a point at distance D and
+        # viewing angle a (the limit of the dense map's sum)
+        a = np.radians(a_deg)
+        px, py = D * np.cos(a), D * np.sin(a)
+        return np.abs(np.arctan2(py, px - S / 2) - np.arctan2(py, px + S / 2))
+
+    rows = []
+    for mu in (1, 2, 4, 8, 16):
+        t1 = time.perf_counter()
+        P = E.Partition(S, mu, 1.0)
+        vp = P.values_at(X, Y)
+        cpu_s = time.perf_counter() - t1
+        c_paper = E.quantise(vp, levels)
+        c_same = E.quantise(P.values_at(X, Y, subtended), levels)
+        inside = np.hypot(X, Y) < P.d_edges[-1]
+        rows.append({"mu_deg": mu, "cells": P.n_cells(), "d_max_m": float(P.d_edges[-1]), "cpu_s": cpu_s,
+                     "eq6_paper_measure": E.eq6_error(c_dense, c_paper),
+                     "eq6_paper_measure_within_d_max": E.eq6_error(c_dense[inside], c_paper[inside]),
+                     "eq6_same_measure": E.eq6_error(c_dense, c_same),
+                     "eq6_same_measure_within_d_max": E.eq6_error(c_dense[inside], c_same[inside]),
+                     "mean_abs_colour_diff_within_d_max": float(np.mean(np.abs(c_dense[inside] - c_same[inside])))})
+    print(json.dumps({"mode": "equivisible", "workload": "2D, 10 m target, 1024 x 1024 cells over 1 km, no "
+                      "obstacles, 16 levels", "dense_gpu_ms": gpu_ms, "rows": rows}), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -737,9 +796,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "batched", "serve", "large", "gaze"], default="step",
+    ap.add_argument("--mode", choices=["step", "batched", "serve", "large", "gaze", "equivisible"], default="step",
                     help="step: the timed VCM step (default); batched / serve: the batching and serving runs; "
-                         "large: the 100,000-box scene at full size; gaze: recolouring for new gazes")
+                         "large: the 100,000-box scene at full size; gaze: recolouring for new gazes; "
+                         "equivisible: the paper's equi-visible cells against the dense map (Eq. 6)")
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=400)
@@ -758,6 +818,8 @@ def main():
         run_large(args)
     elif args.mode == "gaze":
         run_gaze(args)
+    elif args.mode == "equivisible":
+        run_equivisible(args)
     else:
         run_gpu(args)
 
