@@ -482,6 +482,19 @@ def run_batched(args):
     tuned = ctx.vcm_autotune(samples)
     tune_s = time.perf_counter() - t0
     res["persistent_batch"] = timed(batch)
+    # roofline of the batched launch: slab-test operations counted on the
+    # device over the batch's time (which also holds the small prologue and
+    # colour kernels, so the fraction is a lower bound)
+    from paper_1310_7297_gb300 import stats_from_tensor
+    batch()
+    torch.cuda.synchronize()
+    per = [stats_from_tensor(st[i * STATS_BYTES:(i + 1) * STATS_BYTES]) for i in range(len(reqs))]
+    ops = sum(p["slab_tests"] * OPS_PER_ROW_TEST + p["corner_tests"] * OPS_PER_CORNER_TEST for p in per)
+    props = torch.cuda.get_device_properties(dev)
+    peak = alu_peak_ops(props.multi_processor_count, float(peaks().get("sm_max_mhz", 2070.0)))
+    achieved = ops / (res["persistent_batch"]["ms"] / 1e3)
+    res["persistent_batch"]["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                                           "unit": "Tops/s", "frac": achieved / peak}
     res["one_per_launch"] = timed(singles)
     print(json.dumps({"mode": "batched", "metric": METRIC, "unit": UNIT, "requests": len(reqs), "boxes": scene.n,
                       "segments": seg, "autotune_s": tune_s, "tuned_shapes": sorted(set(map(tuple, tuned))),

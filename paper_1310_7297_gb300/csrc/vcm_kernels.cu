@@ -930,6 +930,11 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         const int ix0 = tx * R.tile_x, ix1 = min(R.nx, ix0 + R.tile_x);
         const int iy0 = ty * R.tile_y, iy1 = min(R.ny, iy0 + R.tile_y);
         const int tw = ix1 - ix0, tn = tw * (iy1 - iy0);
+        // row of a tile index vi < 1024 in a row of tw <= 256: the float
+        // product is within 1e-6 of vi / tw, whose fraction is 0.5 / tw away
+        // from an integer, so the truncation is exact (and cheaper than an
+        // integer division)
+        const float inv_tw = 1.0f / (float)tw;
         const float zq = R.z_coord[layer];
         const bool want_bits = (R.flags & VCM_EMIT_BITS) && R.bits_out;
 
@@ -1248,7 +1253,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         if (viewer) {
             // viewer-centric: threads take cells, one segment each
             for (int vi = tid; vi < tn; vi += kThreads) {
-                const int ix = ix0 + vi % tw, iy = iy0 + vi / tw;
+                const int ry = (int)(((float)vi + 0.5f) * inv_tw), ix = ix0 + vi - ry * tw, iy = iy0 + ry;
                 const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
                 bool blocked;
                 const float v = viewer_cell(R, s_box, n_smem, spill, count, gbox, R.x_coord[ix], R.y_coord[iy],
@@ -1278,7 +1283,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 long long vp = 0;
                 bool active = false, behind = false, full = false;
                 if (vi < tn) {
-                    const int ix = ix0 + vi % tw, iy = iy0 + vi / tw;
+                    const int ry = (int)(((float)vi + 0.5f) * inv_tw), ix = ix0 + vi - ry * tw, iy = iy0 + ry;
                     vp = ((long long)layer * R.ny + iy) * R.nx + ix;
                     const float qx = R.x_coord[ix], qy = R.y_coord[iy];
                     const float qu = R.au == 0 ? qx : (R.au == 1 ? qy : zq);
@@ -1322,7 +1327,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 break;
             {
                 const int vi = s_und[k];
-                const int ix = ix0 + vi % tw, iy = iy0 + vi / tw;
+                const int ry = (int)(((float)vi + 0.5f) * inv_tw), ix = ix0 + vi - ry * tw, iy = iy0 + ry;
                 const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
                 const float qx = R.x_coord[ix], qy = R.y_coord[iy];
                 const float qu = R.au == 0 ? qx : (R.au == 1 ? qy : zq);
