@@ -32,13 +32,18 @@ if ROOT not in sys.path:
 METRIC = "viewpoint-patch occlusion tests/sec and VCM cells/sec at ≤1e-5 rel err; p50/p99 latency"
 UNIT = "segments/s"
 WORKLOAD = "3D plain VCM: 512x512 viewpoints x 5 layers, 5,000 mixture boxes over 2 km, 20x10 m target, 32x16 patches"
-# Lane-level operations the tile kernel issues per segment/box slab test:
-# a row test of the sweep is 2 FMUL (w interval), 3 FMNMX (entry/exit),
-# 1 FADD (margin), 1 FSETP (band compare); a corner test of the
-# one-box-blocks-all check is a quarter of its ~60 operations per box
-# (5 reciprocals, 6 FADD, 10 SEL, 10 FMUL, 4 x (4 FMNMX, FADD, FSETP)).
-OPS_PER_ROW_TEST = 7
-OPS_PER_CORNER_TEST = 15
+# Algorithmic work of one segment/box slab test: per axis the entry and exit
+# parameters (a multiply each; the differences to the box faces are shared
+# per viewpoint and box), their min/max, and the running max of entries and
+# min of exits, then one compare: 6 FMUL + 12 FMNMX + 1 compare = 19 FP32
+# operations in 3D, 13 in 2D.  Every test the tile kernel counts (row tests
+# of the sweep, corner tests of the one-box checks) decides one
+# segment/box pair.  The separable sweep itself issues only ~7 lane
+# operations per row test, sharing the u and n parts across a column's rows;
+# those are reported beside the fraction.
+OPS_PER_SLAB_TEST = {3: 19, 2: 13}
+ISSUED_OPS_PER_ROW_TEST = 7
+ISSUED_OPS_PER_CORNER_TEST = 15
 L2_FLUSH_BYTES = 512 << 20
 # kernels of ours that one step launches: k_prologue, k_tiles, k_quantise
 LAUNCHES_PER_STEP = 3
@@ -378,7 +383,9 @@ def run_gpu(args):
         peak = alu_peak_ops(sm_count, max_mhz)
         kern_avg_s = float(np.mean(kern_ms)) / 1e3
         units = stats["slab_tests"] + stats["corner_tests"]
-        achieved = (stats["slab_tests"] * OPS_PER_ROW_TEST + stats["corner_tests"] * OPS_PER_CORNER_TEST) / kern_avg_s
+        achieved = units * OPS_PER_SLAB_TEST[req["dims"]] / kern_avg_s
+        issued = (stats["slab_tests"] * ISSUED_OPS_PER_ROW_TEST +
+                  stats["corner_tests"] * ISSUED_OPS_PER_CORNER_TEST) / kern_avg_s
         value = world * seg * K / (total_ms / 1e3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -390,7 +397,10 @@ def run_gpu(args):
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(),
                          "kernel": "k_tiles", "work_unit": "segment/box slab test",
-                         "ops_per_unit": {"row_test": OPS_PER_ROW_TEST, "corner_test": OPS_PER_CORNER_TEST},
+                         "ops_per_unit": OPS_PER_SLAB_TEST[req["dims"]],
+                         "issued_slab_ops": {"value": issued / 1e12, "frac": issued / peak,
+                                             "ops_per_row_test": ISSUED_OPS_PER_ROW_TEST,
+                                             "ops_per_corner_test": ISSUED_OPS_PER_CORNER_TEST},
                          "units_per_launch": units,
                          "peak_basis": "%d SMs x 128 lane-instr/clk x %.0f MHz (issue limit)" % (sm_count, max_mhz)},
             "stats": {"slab_tests": stats["slab_tests"], "corner_tests": stats["corner_tests"],
@@ -489,7 +499,7 @@ def run_batched(args):
     batch()
     torch.cuda.synchronize()
     per = [stats_from_tensor(st[i * STATS_BYTES:(i + 1) * STATS_BYTES]) for i in range(len(reqs))]
-    ops = sum(p["slab_tests"] * OPS_PER_ROW_TEST + p["corner_tests"] * OPS_PER_CORNER_TEST for p in per)
+    ops = sum((p["slab_tests"] + p["corner_tests"]) * OPS_PER_SLAB_TEST[r["dims"]] for p, r in zip(per, reqs))
     props = torch.cuda.get_device_properties(dev)
     peak = alu_peak_ops(props.multi_processor_count, float(peaks().get("sm_max_mhz", 2070.0)))
     achieved = ops / (res["persistent_batch"]["ms"] / 1e3)
