@@ -656,3 +656,23 @@ def test_recolor_argument_errors(ctx):
         ctx.vcm_recolor(req, None, 1, None, 1, None)
     with pytest.raises(VcmError, match="VCM_E_ARG"):
         ctx.recolor(dict(req, fov_deg=-5.0), bits)
+
+
+@pytest.mark.parametrize("case", ["two_sided", "fov_strict", "plain_bits"])
+def test_many_patch_requests_take_the_whole_tile_check(ctx, case):
+    """Requests of >= 1,024 patches run the tile kernel's instantiation with
+    the whole-tile check (and, when two-sided or coned, the one with both);
+    values, bits and colors still match the oracle."""
+    from paper_1310_7297_gb300 import VCM_STRICT, VCM_TWO_SIDED
+
+    sc, req = synth.workload_3d(seed=71, grid=24, layers=2, patches=(64, 32), n_boxes=250, half_m=300.0,
+                                n_components=4, sigma_m=(40.0, 100.0))
+    load(ctx, sc)
+    r = dict(req)
+    if case == "two_sided":
+        r.update(flags=VCM_TWO_SIDED)
+    elif case == "fov_strict":
+        r.update(flags=VCM_STRICT, fov_deg=140.0, gaze=[-0.3, 1.0, 0.0])
+    gv, gb, st, err, mism = full_parity(ctx, sc, r)
+    assert gb.any() and (gv > 0).sum() > 10
+    assert st["corner_tests"] > 0
