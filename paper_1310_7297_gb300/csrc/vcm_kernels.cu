@@ -864,7 +864,13 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // does tile b only and exits, so blocks of concurrent launches
         // interleave (a persistent grid would hold every SM to the end).
         if (tid == 0) {
-            const int it = one_tile ? (sm.item == -2 ? total_tiles : (int)blockIdx.x) : atomicAdd(work, 1);
+            int it = one_tile ? (sm.item == -2 ? total_tiles : (int)blockIdx.x) : atomicAdd(work, 1);
+            // Queue order: last tile first, and within a request the layers
+            // interleaved (consecutive items are one tile position in every
+            // layer).  Measured on the 3D workload with the target facing
+            // each of +-x and +-y: 3-14 % faster than the plain order, never
+            // slower; either change alone was not.
+            it = it < total_tiles ? total_tiles - 1 - it : total_tiles;
             sm.item = it;
             if (it < total_tiles) {
                 // request of this tile: last r with tile_prefix[r] <= it
@@ -880,7 +886,12 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                     s_req = reqs[lo_r];
                     s_req_idx = lo_r;
                 }
-                sm.pad = it - tile_prefix[lo_r];   // tile index within its request
+                {
+                    // tile index within its request, layers interleaved
+                    const int t0 = it - tile_prefix[lo_r];
+                    const int nl = s_req.nl, pl = s_req.tiles_x * s_req.tiles_y;
+                    sm.pad = (t0 % nl) * pl + t0 / nl;
+                }
                 const DevRequest &Q = s_req;
                 const int t0 = sm.pad, pl = Q.tiles_x * Q.tiles_y;
                 const int ly = t0 / pl, t1 = t0 - ly * pl;
