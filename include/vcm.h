@@ -331,9 +331,10 @@ vcm_status vcm_recolor(vcm_ctx *ctx, const vcm_request *req, const uint32_t *d_b
 /* ---- profiling --------------------------------------------------------- */
 
 /* Record two caller-created CUDA events (cudaEvent_t) on the launch stream
- * immediately before and after the tile kernel of every later direct-path
- * launch (vcm_compute, vcm_compute_batch) and the recolour kernel of every
- * later vcm_recolor; NULL, NULL stops.  The events must outlive their use. */
+ * immediately before and after the tile kernel (both of its passes) of every
+ * later direct-path launch (vcm_compute, vcm_compute_batch) and the recolour
+ * kernel of every later vcm_recolor; NULL, NULL stops.  The events must
+ * outlive their use. */
 vcm_status vcm_set_timing_events(vcm_ctx *ctx, void *before_tiles, void *after_tiles);
 
 #ifdef __cplusplus

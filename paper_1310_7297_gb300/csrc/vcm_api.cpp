@@ -631,8 +631,8 @@ vcm_status ensure_slot(vcm_ctx *ctx, Slot &s, size_t desc_bytes, size_t n_stats,
         CUDA_TRY(cudaStreamSynchronize(s.stream));
     if (!s.desc_copied)
         CUDA_TRY(cudaEventCreateWithFlags(&s.desc_copied, cudaEventDisableTiming));
-    if (!s.d_work)
-        CUDA_TRY(cudaMalloc(&s.d_work, 256));
+    if (!s.d_work)   // tile-queue counters (zeroed by k_prologue) and the work-sharing arena
+        CUDA_TRY(cudaMalloc(&s.d_work, kWorkBytes));
     if (desc_bytes > s.desc_cap) {
         size_t cap = std::max<size_t>(desc_bytes * 2, 1 << 16);
         if (s.d_desc) cudaFree(s.d_desc);
@@ -749,7 +749,8 @@ vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *st
     if (timed && ctx->ev_before)
         CUDA_TRY(cudaEventRecord(ctx->ev_before, stream));
     CUDA_TRY(launch_tiles(ctx->scene, d_reqs, d_tiles, (int)P.n, P.L.total_tiles, s.d_work, s.d_spill,
-                          P.blocks, P.box_cap, P.extra, P.tile_check, stream, one_tile, s.d_spill_busy));
+                          P.blocks, P.box_cap, P.extra, P.tile_check, stream, one_tile, s.d_spill_busy,
+                          /*share=*/true));
     if (timed && ctx->ev_after)
         CUDA_TRY(cudaEventRecord(ctx->ev_after, stream));
     CUDA_TRY(launch_quantise(d_reqs, d_vps, (int)P.n, P.L.total_vp, stream));
@@ -1836,7 +1837,7 @@ vcm_status vcm_compute_static(const float *lo, const float *hi, uint32_t n_boxes
         float4 *s_cell_lo = reinterpret_cast<float4 *>(take((size_t)n_cells * sizeof(float4)));
         float4 *s_cell_hi = reinterpret_cast<float4 *>(take((size_t)n_cells * sizeof(float4)));
         unsigned *s_overhang = reinterpret_cast<unsigned *>(take(sizeof(unsigned)));
-        int *s_work = reinterpret_cast<int *>(take(sizeof(int)));
+        int *s_work = reinterpret_cast<int *>(take(kWorkHeader * sizeof(int)));   // counters only: no sharing
         int *s_spill = reinterpret_cast<int *>(take(256));   // never written: lists fit box_cap
         char *s_desc = take(lay.bytes);
         if (off > cap)

@@ -22,6 +22,27 @@ constexpr int kPyramidMinCount = 64;      // candidate lists longer than this ge
 constexpr int kMaxTileViewpoints = 1024;  // viewpoints in one tile (tile_x * tile_y)
 constexpr int kClaimRounds = 4096;        // bounded retries of a spill-region claim (2 us pauses)
 
+// Work sharing of the persistent tile kernel, in two passes.  In the first,
+// a tile whose one-box check leaves at least kMinPublish viewpoints open
+// publishes them, up to kChunkVp at a time, as chunks; the second pass (a
+// second launch of the same kernel) sweeps the chunks.  The work buffer of a
+// launch holds kWorkHeader counters (next tile, records, chunks published,
+// chunks taken) and then the arena:
+//   chunk[kChunkCap][2 + kChunkVp]       record index, count, viewpoints (tile-local)
+//   record[kRecCap][2 + kRecBoxes]       queue item, candidate count, box ids
+// A launch whose tiles would publish more than the caps keeps the rest in
+// the owning blocks.
+constexpr int kChunkVp = 16;
+constexpr int kMinPublish = 8;
+constexpr int kRecBoxes = 128;
+constexpr int kChunkCap = 65536;
+constexpr int kRecCap = 16384;
+constexpr int kWorkHeader = 64;   // ints before the arena (256 bytes)
+constexpr size_t kChunkOff = 0;
+constexpr size_t kRecOff = kChunkOff + (size_t)kChunkCap * (2 + kChunkVp);
+constexpr size_t kArenaInts = kRecOff + (size_t)kRecCap * (2 + kRecBoxes);
+constexpr size_t kWorkBytes = (kWorkHeader + kArenaInts) * sizeof(int);
+
 inline size_t tiles_smem_bytes(int box_cap) { return (size_t)box_cap * (32 + 4); }
 
 // Device view of the scene and its uniform-grid index.  Boxes are sorted by
@@ -93,10 +114,13 @@ cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, 
 // cone: it selects the tile kernel's instantiation that handles them.
 // `tile_check` selects the instantiation with the whole-tile check (any
 // launch may use either; it pays when every request has many patches).
+// `share` (persistent launches only): d_work is kWorkBytes long, and a second
+// launch of the kernel works the open viewpoints that expensive tiles of the
+// first published there.
 cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
                          int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
                          int box_cap, bool extra, bool tile_check, cudaStream_t stream, bool one_tile = false,
-                         int *d_spill_busy = nullptr);
+                         int *d_spill_busy = nullptr, bool share = false);
 // Colors and edge counts for all viewpoints of n_req requests (grid over the
 // concatenated viewpoints, `d_vp_prefix` = exclusive prefix, n_req + 1).
 cudaError_t launch_quantise(const DevRequest *d_reqs, const long long *d_vp_prefix, int n_req,
@@ -109,7 +133,8 @@ cudaError_t launch_quantise(const DevRequest *d_reqs, const long long *d_vp_pref
 cudaError_t launch_recolor(const DevRequest *d_req, long long n_vp, int sm_count, int *d_list, int *d_n_list,
                            cudaStream_t stream);
 
-// Zero the tile-queue counter d_work, every request's vcm_stats and, when
+// Zero the tile-queue counters (d_work[0..kWorkHeader)), every request's
+// vcm_stats and, when
 // any_bits, the occlusion-bit buffers of the requests with VCM_EMIT_BITS.
 cudaError_t launch_prologue(const DevRequest *d_reqs, int n_req, int *d_work, bool any_bits, cudaStream_t stream);
 

@@ -248,6 +248,8 @@ struct TileSmem {
     int item;
     int pad;
     int n_und;
+    int helper;   // chunk this block took (-1: a tile from the queue)
+    int pub[3];   // record, first chunk and chunks published
 };
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
@@ -809,7 +811,7 @@ template <bool EXTRA, bool TILE_CHECK>
 __global__ void __launch_bounds__(kThreads, 5)
 k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict__ tile_prefix,
         int n_req, int total_tiles, int *__restrict__ work, int *__restrict__ spill_all, int box_cap,
-        int one_tile, int *__restrict__ spill_busy, int spill_slots)
+        int one_tile, int *__restrict__ spill_busy, int spill_slots, int share)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *s_box = reinterpret_cast<float4 *>(smem_raw);
@@ -863,15 +865,30 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // hull points (one barrier for all of it).  With one_tile, block b
         // does tile b only and exits, so blocks of concurrent launches
         // interleave (a persistent grid would hold every SM to the end).
+        // The second pass (share == 2) takes the chunks the first published,
+        // in order, and no tiles.
         if (tid == 0) {
-            int it = one_tile ? (sm.item == -2 ? total_tiles : (int)blockIdx.x) : atomicAdd(work, 1);
-            // Queue order: last tile first, and within a request the layers
-            // interleaved (consecutive items are one tile position in every
-            // layer).  Measured on the 3D workload with the target facing
-            // each of +-x and +-y: 3-14 % faster than the plain order, never
-            // slower; either change alone was not.
-            it = it < total_tiles ? total_tiles - 1 - it : total_tiles;
+            int took = -1, it;
+            if (share == 2) {
+                const int h = atomicAdd(work + 3, 1);
+                took = h < min(__ldcg(work + 2), kChunkCap) ? h : -1;
+            }
+            if (took >= 0) {
+                const int rec = __ldcg(work + kWorkHeader + kChunkOff + (size_t)(2 + kChunkVp) * took);
+                it = __ldcg(work + kWorkHeader + kRecOff + (size_t)(2 + kRecBoxes) * rec);
+            } else if (share == 2) {
+                it = total_tiles;
+            } else {
+                it = one_tile ? (sm.item == -2 ? total_tiles : (int)blockIdx.x) : atomicAdd(work, 1);
+                // Queue order: last tile first, and within a request the
+                // layers interleaved (consecutive items are one tile position
+                // in every layer).  Measured on the 3D workload with the
+                // target facing each of +-x and +-y: 3-14 % faster than the
+                // plain order, never slower; either change alone was not.
+                it = it < total_tiles ? total_tiles - 1 - it : total_tiles;
+            }
             sm.item = it;
+            sm.helper = took;
             if (it < total_tiles) {
                 // request of this tile: last r with tile_prefix[r] <= it
                 int lo_r = 0, hi_r = n_req - 1;
@@ -932,6 +949,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         const int item = sm.item;
         if (item >= total_tiles)
             break;
+        const int helper = sm.helper;
         const DevRequest &R = s_req;
         const int t = sm.pad;
         const int per_layer = R.tiles_x * R.tiles_y;
@@ -973,8 +991,10 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         }
 
         const int np = (R.dims == 3) ? 8 : 6;
-        hull_planes(R.dims, s_pts, np, sm);
-        __syncthreads();
+        if (helper < 0) {
+            hull_planes(R.dims, s_pts, np, sm);
+            __syncthreads();
+        }
         const int n_planes = min(sm.n_planes, kMaxPlanes);
 
         // walk the grid cells under the hull's footprint.  In the xy plane
@@ -987,7 +1007,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // is spanned by the interval's two ends.  Rows are taken 128 at a
         // time: one thread finds a row's span, a block scan lays the spans
         // end to end, and the threads share out the cells.
-        {
+        if (helper < 0) {
             float ax0 = s_pts[0][0], ax1 = ax0, ay0 = s_pts[0][1], ay1 = ay0;
             for (int l = 1; l < 4; ++l) {
                 ax0 = fminf(ax0, s_pts[l][0]); ax1 = fmaxf(ax1, s_pts[l][0]);
@@ -1133,6 +1153,20 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                     s_npass = 0;
                 __syncthreads();   // the next rows reuse the span arrays
             }
+        } else {
+            // a chunk: the owner's candidate list, in the owner's order, and
+            // the chunk's viewpoints
+            const int *ch = work + kWorkHeader + kChunkOff + (size_t)(2 + kChunkVp) * helper;
+            const int *rec = work + kWorkHeader + kRecOff + (size_t)(2 + kRecBoxes) * __ldcg(ch);
+            const int cnt = __ldcg(rec + 1), n_ch = __ldcg(ch + 1);
+            for (int i = tid; i < cnt; i += kThreads)
+                s_ids[i] = __ldcg(rec + 2 + i);
+            for (int i = tid; i < n_ch; i += kThreads)
+                s_und[i] = __ldcg(ch + 2 + i);
+            if (tid == 0) {
+                sm.count = cnt;
+                sm.n_und = n_ch;
+            }
         }
         __syncthreads();
         const int count = sm.count;
@@ -1142,7 +1176,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // most sightlines, so the all-blocked exits come early.  Keys are the
         // squared footprint distance from the tile centre (a positive float,
         // so its bits order like the value) above the sorted box index.
-        if (n_smem > 1) {
+        if (helper < 0 && n_smem > 1) {
             const float cx = 0.5f * (R.x_coord[ix0] + R.x_coord[ix1 - 1]);
             const float cy = 0.5f * (R.y_coord[iy0] + R.y_coord[iy1 - 1]);
             auto key_of = [&](int i) {
@@ -1238,7 +1272,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // target plane then covers every patch of every viewpoint.  Threads
         // take the nearest candidates, one each, against all 16 segments.
         bool tile_blocked = false;
-        if (TILE_CHECK && !viewer) {
+        if (TILE_CHECK && !viewer && helper < 0) {
             bool full = false;
             if (tid < min(n_smem, kThreads)) {
                 full = box_blocks_tile(R, s_box[2 * tid], s_box[2 * tid + 1], R.x_coord[ix0], R.x_coord[ix1 - 1],
@@ -1280,7 +1314,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // is almost always among them); the viewpoints it leaves open are
         // listed and then taken one per warp for the check over the 32
         // nearest and the separable sweep.
-        for (; !viewer && !tile_blocked;) {
+        for (; !viewer && !tile_blocked && helper < 0;) {
             int base = 0;
             if (lane == 0)
                 base = atomicAdd(&s_next, 4);
@@ -1327,8 +1361,49 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             }
         }
         __syncthreads();
+        int n_und = (viewer || tile_blocked) ? 0 : sm.n_und;
+        // Work sharing, first pass (share == 1): a tile with at least
+        // kMinPublish open viewpoints publishes them, in chunks of up to
+        // kChunkVp, with its candidate list (when the list is staged whole and
+        // fits a record), and the second pass sweeps them.  Without it a few
+        // hundred tiles of mostly visible viewpoints set the end of the launch
+        // (3D workload: 100-290 us each against 17 us for the median tile).
+        // Chunks past the arena's caps stay with the tile.
+        if (share == 1 && n_und >= kMinPublish && count <= n_smem && count <= kRecBoxes) {
+            int *arena = work + kWorkHeader;
+            if (tid == 0) {
+                const int want = (n_und + kChunkVp - 1) / kChunkVp;
+                const int rec = atomicAdd(work + 1, 1);
+                int base = 0, got = 0;
+                if (rec < kRecCap) {
+                    base = atomicAdd(work + 2, want);
+                    got = max(0, min(want, kChunkCap - base));
+                }
+                sm.pub[0] = rec;
+                sm.pub[1] = base;
+                sm.pub[2] = got;
+                s_next2 = min(n_und, got * kChunkVp);   // the tile keeps the rest
+            }
+            __syncthreads();
+            const int pub_n = sm.pub[2];
+            if (pub_n > 0) {
+                const int rec = sm.pub[0], pub_base = sm.pub[1];
+                int *rp = arena + kRecOff + (size_t)(2 + kRecBoxes) * rec;
+                if (tid == 0) {
+                    rp[0] = item;
+                    rp[1] = count;
+                }
+                for (int i = tid; i < count; i += kThreads)
+                    rp[2 + i] = s_ids[i];
+                for (int i = tid; i < pub_n * (2 + kChunkVp); i += kThreads) {
+                    const int j = i / (2 + kChunkVp), r = i - j * (2 + kChunkVp);
+                    const int n_j = min(kChunkVp, n_und - j * kChunkVp);
+                    arena[kChunkOff + (size_t)(2 + kChunkVp) * (pub_base + j) + r] =
+                        r == 0 ? rec : r == 1 ? n_j : (r - 2 < n_j ? s_und[j * kChunkVp + r - 2] : -1);
+                }
+            }
+        }
         // then the undecided viewpoints, one per warp at a time
-        const int n_und = (viewer || tile_blocked) ? 0 : sm.n_und;
         for (;;) {
             int k = 0;
             if (lane == 0)
@@ -1405,7 +1480,8 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         if (lane == 0 && rechecks)
             atomicAdd(&R.stats->rechecked, (unsigned long long)rechecks);
         if (tid == 0) {
-            atomicAdd(&R.stats->boxes_listed, (unsigned long long)count);
+            if (sm.helper < 0)
+                atomicAdd(&R.stats->boxes_listed, (unsigned long long)count);
             sm.item = -2;   // one_tile: the next round exits
         }
         __syncthreads();
@@ -1421,8 +1497,8 @@ __global__ void k_prologue(const DevRequest *__restrict__ reqs, int n_req, int *
 {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long nt = (long long)gridDim.x * blockDim.x;
-    if (t == 0)
-        *work = 0;
+    if (t < 4)
+        work[t] = 0;   // next tile, records, chunks published, chunks taken
     constexpr int kStatWords = (int)(sizeof(vcm_stats) / sizeof(unsigned));
     for (long long i = t; i < (long long)n_req * kStatWords; i += nt)
         reinterpret_cast<unsigned *>(reqs[i / kStatWords].stats)[i % kStatWords] = 0u;
@@ -1725,7 +1801,7 @@ int tiles_blocks_per_sm(int box_cap)
 cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
                          int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
                          int box_cap, bool extra, bool tile_check, cudaStream_t stream, bool one_tile,
-                         int *d_spill_busy)
+                         int *d_spill_busy, bool share)
 {
     if (total_tiles <= 0)
         return cudaSuccess;
@@ -1740,8 +1816,17 @@ cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int
     }
     auto kernel = extra ? (tile_check ? k_tiles<true, true> : k_tiles<true, false>)
                         : (tile_check ? k_tiles<false, true> : k_tiles<false, false>);
+    share = share && !one_tile;
     kernel<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles, d_work, d_spill,
-                                                    box_cap, one_tile ? 1 : 0, d_spill_busy, slots);
+                                                    box_cap, one_tile ? 1 : 0, d_spill_busy, slots, share ? 1 : 0);
+    if (share) {
+        // the second pass: the chunks the first published
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
+        kernel<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles, d_work,
+                                                        d_spill, box_cap, 0, d_spill_busy, slots, 2);
+    }
     return cudaGetLastError();
 }
 

@@ -9,14 +9,33 @@ from oracle import oracle as O
 V_RTOL = 1e-5   # relative tolerance on visibility (float32 path vs float64 oracle)
 
 
+def _stats_bytes():
+    from paper_1310_7297_gb300 import vcm
+
+    return vcm.STATS_BYTES
+
+
 def gpu_run(ctx, req, bits=True):
+    """One request through vcm_compute into outputs prefilled with
+    sentinels (NaN values, colour 255, bit words 0xA5A5A5A5), so that a
+    viewpoint the kernels never write fails the comparison."""
     import torch
 
-    from paper_1310_7297_gb300 import n_viewpoints, stats_from_tensor
+    from paper_1310_7297_gb300 import VCM_EMIT_BITS, n_viewpoints, stats_from_tensor, words
 
-    v, c, b, s = ctx.compute(req, emit_bits=bits)
-    torch.cuda.synchronize()
+    dev = torch.device("cuda", ctx.device)
     n = n_viewpoints(req)
+    req = dict(req)
+    if bits:
+        req["flags"] = req.get("flags", 0) | VCM_EMIT_BITS
+    v = torch.full((n,), float("nan"), dtype=torch.float32, device=dev)
+    c = torch.full((n,), 255, dtype=torch.uint8, device=dev)
+    b = torch.full((n * words(req),), -1515870811, dtype=torch.int32, device=dev) if bits else None
+    s = torch.zeros(_stats_bytes(), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx.vcm_compute(req, v.data_ptr(), c.data_ptr(), b.data_ptr() if b is not None else None, s.data_ptr(),
+                    stream.cuda_stream)
+    torch.cuda.synchronize()
     v = v.cpu().numpy().astype(np.float64)
     c = c.cpu().numpy()
     if bits:

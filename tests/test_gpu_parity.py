@@ -101,6 +101,8 @@ def test_workload_3d_full_size_sampled(ctx):
     load(ctx, sc)
     gv, gc, gb, st = gpu_run(ctx, req, bits=True)
     n = gv.shape[0]
+    # every viewpoint written (outputs start as NaN / colour 255)
+    assert np.isfinite(gv).all() and (gc != 255).all()
     rng = np.random.default_rng(11)
     nz = np.nonzero(gv > 0)[0]
     idx = np.unique(np.concatenate([rng.choice(n, 600, replace=False), rng.choice(nz, 600, replace=False)]))
@@ -277,8 +279,8 @@ def test_batch_equals_single_requests(ctx):
     load(ctx, sc, 50.0)
     singles = [_bits_and_v(ctx, dict(r, flags=1)) for r in reqs]
     dev = torch.device("cuda", 0)
-    vs = [torch.empty(n_viewpoints(r), device=dev) for r in reqs]
-    cs = [torch.empty(n_viewpoints(r), dtype=torch.uint8, device=dev) for r in reqs]
+    vs = [torch.full((n_viewpoints(r),), float("nan"), device=dev) for r in reqs]
+    cs = [torch.full((n_viewpoints(r),), 255, dtype=torch.uint8, device=dev) for r in reqs]
     bs = [torch.empty(n_viewpoints(r) * words(r), dtype=torch.int32, device=dev) for r in reqs]
     st = torch.empty(STATS_BYTES * len(reqs), dtype=torch.uint8, device=dev)
     ctx.vcm_compute_batch([dict(r, flags=1) for r in reqs], [t.data_ptr() for t in vs], [t.data_ptr() for t in cs],
@@ -365,13 +367,20 @@ def test_argument_errors(ctx):
 # ---------------------------------------------------------------------------
 
 def _sampled_bits(ctx, req, idx):
-    """Run a request with bits on the device and bring back only the sampled rows."""
+    """Run a request with bits on the device (values prefilled with NaN) and
+    bring back only the sampled rows."""
     import torch
 
-    from paper_1310_7297_gb300 import n_viewpoints
+    from paper_1310_7297_gb300 import VCM_EMIT_BITS, n_viewpoints, words
 
-    v, c, b, s = ctx.compute(req, emit_bits=True)
     n = n_viewpoints(req)
+    req = dict(req, flags=req.get("flags", 0) | VCM_EMIT_BITS)
+    v = torch.full((n,), float("nan"), device="cuda")
+    c = torch.empty(n, dtype=torch.uint8, device="cuda")
+    b = torch.empty(n * words(req), dtype=torch.int32, device="cuda")
+    s = torch.empty(STATS_BYTES, dtype=torch.uint8, device="cuda")
+    ctx.vcm_compute(req, v.data_ptr(), c.data_ptr(), b.data_ptr(), s.data_ptr(),
+                    torch.cuda.current_stream().cuda_stream)
     t = torch.as_tensor(idx, device=v.device)
     bv = v.index_select(0, t).cpu().numpy().astype(np.float64)
     bb = b.view(n, -1).index_select(0, t).cpu().numpy().view(np.uint32)
@@ -391,6 +400,7 @@ def test_workload_3d_large_full_size_sampled(ctx):
     rng = np.random.default_rng(21)
     idx0 = np.sort(rng.choice(n, 200, replace=False))
     gv0, gb0, v_all = _sampled_bits(ctx, req, idx0)
+    assert np.isfinite(v_all).all()   # every viewpoint written
     nz = np.nonzero(v_all > 0)[0]
     idx1 = np.sort(rng.choice(nz, min(200, nz.size), replace=False))
     idx = np.unique(np.concatenate([idx0, idx1]))
@@ -411,13 +421,15 @@ def test_workload_batched_full_mix_sampled(ctx):
     sc, reqs = synth.workload_batched()
     load(ctx, sc, 50.0)
     dev = torch.device("cuda", 0)
-    vs = [torch.empty(n_viewpoints(r), device=dev) for r in reqs]
-    cs = [torch.empty(n_viewpoints(r), dtype=torch.uint8, device=dev) for r in reqs]
+    vs = [torch.full((n_viewpoints(r),), float("nan"), device=dev) for r in reqs]
+    cs = [torch.full((n_viewpoints(r),), 255, dtype=torch.uint8, device=dev) for r in reqs]
     bs = [torch.empty(n_viewpoints(r) * words(r), dtype=torch.int32, device=dev) for r in reqs]
     st = torch.empty(STATS_BYTES * len(reqs), dtype=torch.uint8, device=dev)
     ctx.vcm_compute_batch([dict(r, flags=1) for r in reqs], [t.data_ptr() for t in vs], [t.data_ptr() for t in cs],
                           [t.data_ptr() for t in bs], st.data_ptr(), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
+    # every viewpoint of every request written
+    assert all(bool(torch.isfinite(t).all()) for t in vs) and all(bool((t != 255).all()) for t in cs)
     rng = np.random.default_rng(5)
     for k in rng.choice(len(reqs), 8, replace=False):
         r = reqs[k]
