@@ -434,9 +434,10 @@ struct Slot {
     std::vector<std::shared_ptr<::Ticket>> inflight;
     bool posted = false;
     std::thread waiter;
-    // graph of the device work of one batched launch
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    // graphs of the device work of one batched launch, one per launch form
+    // (0: one block per tile, 1: persistent with the chunk pass)
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
     size_t graph_desc_bytes = 0;
 };
 
@@ -642,13 +643,15 @@ vcm_status ensure_slot(vcm_ctx *ctx, Slot &s, size_t desc_bytes, size_t n_stats,
         CUDA_TRY(cudaMalloc(&s.d_desc, cap));
         CUDA_TRY(cudaMallocHost(&s.h_desc, cap));
         s.desc_cap = cap;
-        if (s.exec) {
-            cudaGraphExecDestroy(s.exec);
-            s.exec = nullptr;
-        }
-        if (s.graph) {
-            cudaGraphDestroy(s.graph);
-            s.graph = nullptr;
+        for (int f = 0; f < 2; ++f) {
+            if (s.exec[f]) {
+                cudaGraphExecDestroy(s.exec[f]);
+                s.exec[f] = nullptr;
+            }
+            if (s.graph[f]) {
+                cudaGraphDestroy(s.graph[f]);
+                s.graph[f] = nullptr;
+            }
         }
     }
     if (spill_need > s.spill_cap) {
@@ -790,26 +793,27 @@ vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *>
     }
     if (e != cudaSuccess)
         return fail(VCM_E_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
-    if (s.exec) {
+    const int f = one_tile ? 0 : 1;
+    if (s.exec[f]) {
         cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(s.exec, g, &info) != cudaSuccess) {
+        if (cudaGraphExecUpdate(s.exec[f], g, &info) != cudaSuccess) {
             cudaGetLastError();
-            cudaGraphExecDestroy(s.exec);
-            s.exec = nullptr;
+            cudaGraphExecDestroy(s.exec[f]);
+            s.exec[f] = nullptr;
         }
     }
-    if (!s.exec) {
-        e = cudaGraphInstantiate(&s.exec, g, 0);
+    if (!s.exec[f]) {
+        e = cudaGraphInstantiate(&s.exec[f], g, 0);
         if (e != cudaSuccess) {
             cudaGraphDestroy(g);
-            s.exec = nullptr;
+            s.exec[f] = nullptr;
             return fail(VCM_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
         }
     }
-    if (s.graph)
-        cudaGraphDestroy(s.graph);
-    s.graph = g;
-    CUDA_TRY(cudaGraphLaunch(s.exec, s.stream));
+    if (s.graph[f])
+        cudaGraphDestroy(s.graph[f]);
+    s.graph[f] = g;
+    CUDA_TRY(cudaGraphLaunch(s.exec[f], s.stream));
     CUDA_TRY(cudaEventRecord(s.desc_copied, s.stream));
     return VCM_OK;
 }
@@ -956,10 +960,13 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
         bits.push_back(t->d_bits);
     }
     vcm_status st = ensure_slot(ctx, s, 0, group.size(), 1, s.stream);
-    // one block per tile even when alone: a persistent grid would shut out
-    // requests that arrive while it runs
+    // One block per tile while other work runs or waits, so that launches of
+    // other slots interleave with it block by block; a group that starts with
+    // nothing else in flight or queued gets the persistent grid and its chunk
+    // pass (a request that arrives meanwhile waits for it).
+    const bool alone = ctx->running_groups == 0 && ctx->queue.empty();
     if (st == VCM_OK)
-        st = enqueue_graph(ctx, s, cs, shapes, v.data(), col.data(), bits.data(), s.d_stats, true);
+        st = enqueue_graph(ctx, s, cs, shapes, v.data(), col.data(), bits.data(), s.d_stats, !alone);
     if (st == VCM_OK) {
         for (size_t i = 0; i < group.size(); ++i) {
             Ticket &t = *group[i];
@@ -1132,8 +1139,10 @@ void stop_scheduler(vcm_ctx *ctx)
 
 void destroy_slot(Slot &s)
 {
-    if (s.exec) cudaGraphExecDestroy(s.exec);
-    if (s.graph) cudaGraphDestroy(s.graph);
+    for (int f = 0; f < 2; ++f) {
+        if (s.exec[f]) cudaGraphExecDestroy(s.exec[f]);
+        if (s.graph[f]) cudaGraphDestroy(s.graph[f]);
+    }
     if (s.d_desc) cudaFree(s.d_desc);
     if (s.h_desc) cudaFreeHost(s.h_desc);
     if (s.d_work) cudaFree(s.d_work);
@@ -1153,8 +1162,8 @@ void destroy_slot(Slot &s)
     s.d_stats = nullptr;
     s.stats_cap = 0;
     s.busy = s.posted = false;
-    s.graph = nullptr;
-    s.exec = nullptr;
+    s.graph[0] = s.graph[1] = nullptr;
+    s.exec[0] = s.exec[1] = nullptr;
 }
 
 vcm_status validate_ctx(vcm_ctx *ctx)
