@@ -753,6 +753,85 @@ def run_gaze(args):
     ctx.close()
 
 
+def run_modes(args):
+    """The visibility variants on the 3D workload (512 x 512 x 5 viewpoints,
+    5,000 boxes, 32 x 16 patches), each timed like the step (inputs resident,
+    L2 flushed between steps) with its ALU roofline, and the CPU oracle on a
+    bounded sample of the same variant: plain (the step), strict (completely
+    visible), a 120 degree field of view, both, a two-sided target, and the
+    viewer-centric map from a viewer at the target's centre (one segment per
+    cell)."""
+    import torch
+
+    import synth
+    from paper_1310_7297_gb300 import VCM_STRICT, VCM_TWO_SIDED, VCM_VIEWER, Context, stats_from_tensor
+    from paper_1310_7297_gb300 import build as B
+    from paper_1310_7297_gb300.vcm import STATS_BYTES
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    scene, req = synth.workload_3d()
+    n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
+    fov = dict(fov_deg=120.0, gaze=[0.0, 1.0, 0.0])
+    g0, gs = [x / 1024 for x in req["grid_origin"]], [x / 1024 for x in req["grid_step"]]
+    viewer = synth.make_request(3, (0.0, 0.0, 30.0), 0, 2, 1.0, 1, g0, gs, (req["grid_nx"], req["grid_ny"]),
+                                layers_m=[z / 1024 for z in req["layer_z"]], height_m=1.0, color_levels=16,
+                                flags=VCM_VIEWER)
+    variants = [("plain", req), ("strict", dict(req, flags=VCM_STRICT)), ("fov120", dict(req, **fov)),
+                ("strict_fov120", dict(req, flags=VCM_STRICT, **fov)), ("two_sided", dict(req, flags=VCM_TWO_SIDED)),
+                ("viewer", viewer)]
+    ctx = Context(0)
+    ctx.load_scene(scene)
+    ctx.vcm_build(0.0)
+    stream = torch.cuda.current_stream(dev)
+    v = torch.empty(n_vp, dtype=torch.float32, device=dev)
+    c = torch.empty(n_vp, dtype=torch.uint8, device=dev)
+    st = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    pk = peaks()
+    max_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak = alu_peak_ops(torch.cuda.get_device_properties(dev).multi_processor_count, max_mhz)
+    results = []
+    for name, r in variants:
+        P = 1 if r.get("flags", 0) & VCM_VIEWER else r["patches_u"] * r["patches_w"]
+        for _ in range(max(3, args.warmup)):
+            ctx.vcm_compute(r, v.data_ptr(), c.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        kb, ka = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kb.record(stream)   # torch creates an event's handle on its first record
+        ka.record(stream)
+        torch.cuda.synchronize()
+        step, kern = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ctx.vcm_set_timing_events(kb, ka)
+            a.record(stream)
+            ctx.vcm_compute(r, v.data_ptr(), c.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ctx.vcm_set_timing_events(None, None)
+            step.append(a.elapsed_time(b))
+            kern.append(kb.elapsed_time(ka))
+        stats = stats_from_tensor(st)
+        ms, k_ms = float(np.mean(step)), float(np.mean(kern))
+        ops = (stats["slab_tests"] + stats["corner_tests"]) * OPS_PER_SLAB_TEST[r["dims"]]
+        row = {"name": name, "flags": int(r.get("flags", 0)), "ms_per_step": ms, "kernel_ms": k_ms,
+               "segments_per_s": n_vp * P / (ms / 1e3), "cells_per_s": n_vp / (ms / 1e3),
+               "nonzero_cells": int((v > 0).sum().item()),
+               "roofline": {"bound": "alu", "achieved": ops / (k_ms / 1e3) / 1e12, "peak": peak / 1e12,
+                            "unit": "Tops/s", "frac": ops / (k_ms / 1e3) / peak}}
+        if not args.no_cpu_baseline:
+            o = oracle_rate(scene, r, max(1.0, args.cpu_seconds / len(variants)), seed=len(results))
+            row["cpu_oracle"] = {"segments_per_s": o["cells_per_s"] * P, "cells_per_s": o["cells_per_s"],
+                                 "cores": o["cores"], "sample": "%d random viewpoints, %.1f s" % (o["viewpoints"],
+                                                                                               o["seconds"])}
+        results.append(row)
+    print(json.dumps({"mode": "modes", "workload": WORKLOAD, "steps": args.steps,
+                      "l2": "512 MB buffer written between timed steps", "results": results}), flush=True)
+    ctx.close()
+
+
 def run_equivisible(args):
     """The paper's own equi-visible colouring (distance and angle partition,
     a colour per cell from its centre; CPU) against the dense GPU map of the
@@ -820,10 +899,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "batched", "serve", "large", "gaze", "equivisible"], default="step",
+    ap.add_argument("--mode", choices=["step", "batched", "serve", "large", "gaze", "equivisible", "modes"],
+                    default="step",
                     help="step: the timed VCM step (default); batched / serve: the batching and serving runs; "
                          "large: the 100,000-box scene at full size; gaze: recolouring for new gazes; "
-                         "equivisible: the paper's equi-visible cells against the dense map (Eq. 6)")
+                         "equivisible: the paper's equi-visible cells against the dense map (Eq. 6); "
+                         "modes: strict, field of view, two-sided and viewer-centric variants of the step")
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=400)
@@ -844,6 +925,8 @@ def main():
         run_gaze(args)
     elif args.mode == "equivisible":
         run_equivisible(args)
+    elif args.mode == "modes":
+        run_modes(args)
     else:
         run_gpu(args)
 

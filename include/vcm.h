@@ -262,7 +262,8 @@ vcm_status vcm_compute_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, 
 
 /* Time candidate launch shapes on the given sample requests and keep the
  * fastest per request class (patch count bucket); later launches use it.
- * Writes the chosen shape for each sample to out (may be NULL). */
+ * Writes the chosen shape for each sample to out (may be NULL).  Viewer-
+ * centric requests (VCM_VIEWER) keep a fixed shape of 32 x 16 cells. */
 vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vcm_tune *out);
 
 /* Force a launch shape for all later launches (tile_x = 0 restores tuning). */
