@@ -406,6 +406,7 @@ def run_gpu(args):
                          "peak_basis": "%d SMs x 128 lane-instr/clk x %.0f MHz (issue limit)" % (sm_count, max_mhz)},
             "stats": {"slab_tests": stats["slab_tests"], "corner_tests": stats["corner_tests"],
                       "shortcut_viewpoints": stats["shortcut_viewpoints"], "rechecked": stats["rechecked"],
+                      "shared_viewpoints": stats["shared_viewpoints"],
                       "boxes_listed": stats["boxes_listed"], "edge_cells": stats["edge_cells"],
                       "v_ref": stats["v_ref"], "nonzero_cells": int((v > 0).sum().item())},
             "cpu_baseline": cpu,

@@ -152,6 +152,7 @@ typedef struct {
     unsigned long long boxes_listed;   /* sum over tiles of culled candidate-list lengths */
     unsigned long long corner_tests;   /* segment-box tests of the one-box-blocks-all check */
     unsigned long long shortcut_viewpoints;  /* viewpoints decided by that check */
+    unsigned long long shared_viewpoints;    /* open viewpoints handed from their tile to the chunk pass */
 } vcm_stats;
 
 /* Results of a submitted request; all pointers owned by the context. */

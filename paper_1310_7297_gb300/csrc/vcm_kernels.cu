@@ -1383,6 +1383,8 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 sm.pub[1] = base;
                 sm.pub[2] = got;
                 s_next2 = min(n_und, got * kChunkVp);   // the tile keeps the rest
+                if (got > 0)
+                    atomicAdd(&R.stats->shared_viewpoints, (unsigned long long)s_next2);
             }
             __syncthreads();
             const int pub_n = sm.pub[2];

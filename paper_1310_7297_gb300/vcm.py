@@ -61,7 +61,7 @@ class vcm_stats(ctypes.Structure):
                 ("error", ctypes.c_uint32), ("slab_tests", ctypes.c_ulonglong),
                 ("rechecked", ctypes.c_ulonglong), ("segments", ctypes.c_ulonglong),
                 ("boxes_listed", ctypes.c_ulonglong), ("corner_tests", ctypes.c_ulonglong),
-                ("shortcut_viewpoints", ctypes.c_ulonglong)]
+                ("shortcut_viewpoints", ctypes.c_ulonglong), ("shared_viewpoints", ctypes.c_ulonglong)]
 
 
 class vcm_result(ctypes.Structure):
