@@ -180,7 +180,11 @@ typedef struct {
 
 /* Create a context on CUDA device `device`.  mem_budget_bytes bounds the
  * device memory that admitted requests may hold at once (0 = 64 GiB).
- * The context owns the device scene, its index, streams and scratch. */
+ * The context owns the device scene, its index, streams and scratch: per
+ * execution slot (and one for direct calls) a descriptor buffer, a spill
+ * list of n_boxes ints per resident block, and a 13 MB work buffer through
+ * which the blocks of a launch share the open viewpoints of expensive tiles;
+ * none of these count against the budget. */
 vcm_status vcm_ctx_create(int device, size_t mem_budget_bytes, vcm_ctx **out);
 
 /* Wait for all work of the context, then free everything it owns. */
