@@ -183,8 +183,10 @@ def dist_setup():
 # ---------------------------------------------------------------------------
 
 def oracle_rate(scene, req, seconds, seed=0):
-    """Segments/s of the CPU oracle on a seeded random viewpoint sample sized
-    for about `seconds` of work, on all host cores."""
+    """Segments/s of the CPU oracle on seeded random viewpoint samples that
+    add up to about `seconds` of wall time, on all host cores.  A probe sets
+    the first sample's size; further samples (at most four in all) top the
+    time up, each sized from the rate measured so far."""
     from oracle import oracle as O
 
     O.build()
@@ -194,13 +196,19 @@ def oracle_rate(scene, req, seconds, seed=0):
     probe = np.sort(rng.choice(n, 64, replace=False))
     t0 = time.perf_counter()
     O.run(scene, req, indices=probe)
-    dt = time.perf_counter() - t0
-    m = int(min(n, max(64, 64 * seconds / max(dt, 1e-6))))
-    idx = np.sort(rng.choice(n, m, replace=False))
-    t0 = time.perf_counter()
-    O.run(scene, req, indices=idx)
-    dt = time.perf_counter() - t0
-    return {"value": m * P / dt, "cells_per_s": m / dt, "seconds": dt, "viewpoints": m,
+    rate = 64 / max(time.perf_counter() - t0, 1e-6)
+    m_all, t_all = 0, 0.0
+    for _ in range(4):
+        if t_all >= 0.9 * seconds:
+            break
+        m = int(min(n, max(64, rate * (seconds - t_all))))
+        idx = np.sort(rng.choice(n, m, replace=False))
+        t0 = time.perf_counter()
+        O.run(scene, req, indices=idx)
+        t_all += time.perf_counter() - t0
+        m_all += m
+        rate = m_all / t_all
+    return {"value": m_all * P / t_all, "cells_per_s": m_all / t_all, "seconds": t_all, "viewpoints": m_all,
             "cores": O.default_threads()}
 
 
