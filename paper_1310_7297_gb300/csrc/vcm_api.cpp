@@ -376,7 +376,7 @@ class PinnedPool {
     void *get(size_t bytes)
     {
         std::lock_guard<std::mutex> g(mu_);
-        size_t want = std::max<size_t>(4096, (size_t)1 << (64 - __builtin_clzll(std::max<size_t>(bytes, 1) - 1 | 1)));
+        size_t want = std::max<size_t>(4096, (size_t)1 << (64 - __builtin_clzll((std::max<size_t>(bytes, 1) - 1) | 1)));
         auto it = free_.lower_bound(want);
         if (it != free_.end() && it->first <= 2 * want) {
             void *p = it->second;
@@ -441,7 +441,6 @@ struct Slot {
     // everything a form's graph was captured with (parameters, buffers,
     // scene); an equal key replays the graph as it is
     std::vector<unsigned long long> key[2];
-    size_t graph_desc_bytes = 0;
 };
 
 struct Layout {
