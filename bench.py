@@ -762,6 +762,24 @@ def run_gaze(args):
     ctx.close()
 
 
+def mode_variants(req):
+    """(name, request) of each variant `--mode modes` times, derived from a
+    target-centric request: plain, strict, a 120 degree field of view gazing
+    along +y, both, two-sided, and the viewer-centric map over the same grid
+    from a viewer at the target's centre."""
+    import synth
+    from paper_1310_7297_gb300 import VCM_STRICT, VCM_TWO_SIDED, VCM_VIEWER
+
+    fov = dict(fov_deg=120.0, gaze=[0.0, 1.0, 0.0])
+    g0, gs = [x / 1024 for x in req["grid_origin"]], [x / 1024 for x in req["grid_step"]]
+    viewer = synth.make_request(3, tuple(c / 1024 for c in req["center"]), 0, 2, 1.0, 1, g0, gs,
+                                (req["grid_nx"], req["grid_ny"]), layers_m=[z / 1024 for z in req["layer_z"]],
+                                height_m=1.0, color_levels=16, flags=VCM_VIEWER)
+    return [("plain", req), ("strict", dict(req, flags=VCM_STRICT)), ("fov120", dict(req, **fov)),
+            ("strict_fov120", dict(req, flags=VCM_STRICT, **fov)), ("two_sided", dict(req, flags=VCM_TWO_SIDED)),
+            ("viewer", viewer)]
+
+
 def run_modes(args):
     """The visibility variants on the 3D workload (512 x 512 x 5 viewpoints,
     5,000 boxes, 32 x 16 patches), each timed like the step (inputs resident,
@@ -773,7 +791,7 @@ def run_modes(args):
     import torch
 
     import synth
-    from paper_1310_7297_gb300 import VCM_STRICT, VCM_TWO_SIDED, VCM_VIEWER, Context, stats_from_tensor
+    from paper_1310_7297_gb300 import VCM_VIEWER, Context, stats_from_tensor
     from paper_1310_7297_gb300 import build as B
     from paper_1310_7297_gb300.vcm import STATS_BYTES
 
@@ -781,14 +799,7 @@ def run_modes(args):
     dev = torch.device("cuda", 0)
     scene, req = synth.workload_3d()
     n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
-    fov = dict(fov_deg=120.0, gaze=[0.0, 1.0, 0.0])
-    g0, gs = [x / 1024 for x in req["grid_origin"]], [x / 1024 for x in req["grid_step"]]
-    viewer = synth.make_request(3, (0.0, 0.0, 30.0), 0, 2, 1.0, 1, g0, gs, (req["grid_nx"], req["grid_ny"]),
-                                layers_m=[z / 1024 for z in req["layer_z"]], height_m=1.0, color_levels=16,
-                                flags=VCM_VIEWER)
-    variants = [("plain", req), ("strict", dict(req, flags=VCM_STRICT)), ("fov120", dict(req, **fov)),
-                ("strict_fov120", dict(req, flags=VCM_STRICT, **fov)), ("two_sided", dict(req, flags=VCM_TWO_SIDED)),
-                ("viewer", viewer)]
+    variants = mode_variants(req)
     ctx = Context(0)
     ctx.load_scene(scene)
     ctx.vcm_build(0.0)
