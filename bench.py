@@ -1,17 +1,25 @@
 #!/usr/bin/env python3
 """Benchmark of the visibility color map (VCM) path on GB300.
 
-Workload (one step = one whole VCM: grid-index cull, slab tests, visible
-measure, quantisation): the 3D plain VCM - 512 x 512 viewpoints at 1.7 m
-plus 4 layers spaced 10 m, 5,000 boxes (footprints 10-60 m, lognormal
-heights, median 20 m, sigma 0.6, centres from a 16-component Gaussian
-mixture over 2 km x 2 km), a 20 m x 10 m target at 30 m split into 32 x 16
-patches, 16 color levels.  Seeded synthetic inputs stand in for the paper's
-city datasets.
+Headline workload (one step = one whole VCM: grid-index cull, slab tests,
+visible measure, quantisation): the large 3D scene - 100,000 boxes over
+10 km x 10 km (footprints 10-60 m, lognormal heights with median 20 m and
+sigma 0.6, centres from a 64-component Gaussian mixture), one 40 m x 20 m
+target at 30 m split into 64 x 32 patches, 2048 x 2048 viewpoints on 8
+layers from 1.7 m spaced 10 m, a 50 m uniform-grid index, 16 color levels.
+It is the largest of the single-GPU workloads.  Seeded synthetic inputs
+stand in for the paper's city datasets.
+
+The same JSON line carries sub-records, each with its own clock window:
+the 3D workload of 5,000 boxes (512 x 512 x 5 viewpoints, 32 x 16
+patches), the 256-request uneven mix in one persistent launch against one
+launch per request, and serving (Poisson arrivals at 50-2,000 req/s against
+the resident 100,000-box scene) against a FIFO of one launch per request.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
-Under torchrun each rank runs its own full copy of the workload (weak
-scaling, no data-path collective) and the slowest rank's time is reported.
+Under torchrun each rank runs its own full copy of the headline workload
+(weak scaling, no data-path collective) and the slowest rank's time is
+reported; the sub-records run at N = 1 only.
 """
 
 import argparse
@@ -31,7 +39,10 @@ if ROOT not in sys.path:
 
 METRIC = "viewpoint-patch occlusion tests/sec and VCM cells/sec at ≤1e-5 rel err; p50/p99 latency"
 UNIT = "segments/s"
-WORKLOAD = "3D plain VCM: 512x512 viewpoints x 5 layers, 5,000 mixture boxes over 2 km, 20x10 m target, 32x16 patches"
+WORKLOAD = ("3D large scene: 2048x2048 viewpoints x 8 layers, 100,000 mixture boxes over 10 km, "
+            "40x20 m target, 64x32 patches, 50 m grid index")
+WORKLOAD_3D = "3D plain VCM: 512x512 viewpoints x 5 layers, 5,000 mixture boxes over 2 km, 20x10 m target, 32x16 patches"
+GRID_CELL_LARGE_M = 50.0
 # Algorithmic work of one segment/box slab test: per axis the entry and exit
 # parameters (a multiply each; the differences to the box faces are shared
 # per viewpoint and box), their min/max, and the running max of entries and
@@ -68,17 +79,19 @@ def hbm_peak():
     return {"value": 6800.0, "basis": "fallback 6.8 TB/s (no measured peak file)"}
 
 
-PROFILE = os.path.join(ROOT, "profiles", "k_tiles_3d_512x512x5_5000boxes.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_1310_7297_gb300", "csrc", "vcm_kernels.cu")
+PROFILE_LARGE = os.path.join(ROOT, "profiles", "k_tiles_3d_large_2048x2048x8_100000boxes.md")
+PROFILE_3D = os.path.join(ROOT, "profiles", "k_tiles_3d_512x512x5_5000boxes.md")
 
 
-def profiled_traffic():
-    """DRAM bytes per k_tiles launch from the committed ncu summary, or None
-    if the kernel source has changed since that capture."""
+def profiled_traffic(profile):
+    """DRAM bytes per k_tiles launch (both passes) of the workload a
+    committed ncu summary covers, or None if the kernel source has changed
+    since that capture."""
     import hashlib
 
     try:
-        text = open(PROFILE).read()
+        text = open(profile).read()
         digest = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
     except OSError:
         return None
@@ -102,17 +115,20 @@ def alu_peak_ops(sm_count, mhz):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms for the
+    whole run; ``window`` summarises the samples of one timed region."""
 
     FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, uuid=None):
         self.uuid = uuid
         self.proc = None
         self.lines = []
         self.t = None
+        self.lock = threading.Lock()
 
     def start(self):
         try:
@@ -120,19 +136,51 @@ class ClockSampler:
                                           "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
-            return
+            return self
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
+        return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append((time.monotonic(), line.strip()))
+            with self.lock:
+                self.lines.append((time.monotonic(), line.strip()))
 
-    def stop(self, t_from=None, t_to=None):
-        """Summary of the samples taken between t_from and t_to
-        (time.monotonic()); all samples when not given."""
+    def window(self, t_from, t_to, what=""):
+        """Summary of the samples taken between t_from and t_to (monotonic)."""
         if self.proc is None:
             return None
+        # a sample of the last 200 ms may still be in the pipe
+        deadline = time.monotonic() + 0.5
+        while time.monotonic() < deadline:
+            with self.lock:
+                if self.lines and self.lines[-1][0] >= t_to:
+                    break
+            time.sleep(0.05)
+        with self.lock:
+            lines = list(self.lines)
+        rows = []
+        for ts, l in lines:
+            if ts < t_from or ts > t_to:
+                continue
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 9 or (self.uuid and self.uuid not in parts[0]):
+                continue
+            rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = sorted({self.NAMES[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        out = {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": reasons, "samples": len(rows)}
+        if what:
+            out["window"] = "%.2f s: %s" % (t_to - t_from, what)
+        return out
+
+    def stop(self):
+        if self.proc is None:
+            return
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -140,24 +188,6 @@ class ClockSampler:
             self.proc.kill()
         if self.t:
             self.t.join(timeout=2)
-        rows = []
-        for ts, l in self.lines:
-            if (t_from is not None and ts < t_from) or (t_to is not None and ts > t_to):
-                continue
-            parts = [x.strip() for x in l.split(",")]
-            if len(parts) < 9:
-                continue
-            if self.uuid and self.uuid not in parts[0]:
-                continue
-            rows.append(parts)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
 
 
 def reduce_max(x, pg, device=None):
@@ -178,25 +208,35 @@ def dist_setup():
     return world, rank, local
 
 
+def headline_workload():
+    import synth
+
+    return synth.workload_3d_large()
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-def oracle_rate(scene, req, seconds, seed=0):
+def oracle_rate(scene, req, seconds, seed=0, rate_hint=None):
     """Segments/s of the CPU oracle on seeded random viewpoint samples that
-    add up to about `seconds` of wall time, on all host cores.  A probe sets
-    the first sample's size; further samples (at most four in all) top the
-    time up, each sized from the rate measured so far."""
+    add up to about `seconds` of wall time, on all host cores.  A probe of
+    64 viewpoints (skipped when a viewpoint rate is given) sets the first
+    sample's size; further samples (at most four in all) top the time up,
+    each sized from the rate measured so far."""
     from oracle import oracle as O
 
     O.build()
     n = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
     P = req["patches_u"] * req["patches_w"]
     rng = np.random.default_rng(seed)
-    probe = np.sort(rng.choice(n, 64, replace=False))
-    t0 = time.perf_counter()
-    O.run(scene, req, indices=probe)
-    rate = 64 / max(time.perf_counter() - t0, 1e-6)
+    if rate_hint:
+        rate = float(rate_hint)
+    else:
+        probe = np.sort(rng.choice(n, min(n, 64), replace=False))
+        t0 = time.perf_counter()
+        O.run(scene, req, indices=probe)
+        rate = probe.size / max(time.perf_counter() - t0, 1e-6)
     m_all, t_all = 0, 0.0
     for _ in range(4):
         if t_all >= 0.9 * seconds:
@@ -212,19 +252,31 @@ def oracle_rate(scene, req, seconds, seed=0):
             "cores": O.default_threads()}
 
 
+def config_dict(scene, req, workload=WORKLOAD, grid_cell_m=GRID_CELL_LARGE_M):
+    n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
+    return {"workload": workload, "viewpoints": n_vp, "grid": [req["grid_nx"], req["grid_ny"]],
+            "layers_m": [z / 1024 for z in req["layer_z"]], "patches": [req["patches_u"], req["patches_w"]],
+            "boxes": scene.n, "scene_digest": scene.digest(), "color_levels": req["color_levels"],
+            "grid_index_cell_m": grid_cell_m,
+            "segments_per_step": n_vp * req["patches_u"] * req["patches_w"],
+            "l2": "512 MB buffer written between timed steps (outputs of 168 MB also exceed L2)",
+            "parallelism": "replicas"}
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    import synth
-
-    scene, req = synth.workload_3d()
-    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    scene, req = headline_workload()
+    # bounded: the whole run takes about 90 s of oracle time
+    per_step = max(1.5, 90.0 / max(1, args.steps + args.warmup))
+    rate = None
     for i in range(args.warmup):
-        oracle_rate(scene, req, per_step / 4, seed=100 + i)
+        rate = oracle_rate(scene, req, per_step / 2, seed=100 + i, rate_hint=rate)["cells_per_s"]
     rates, secs, vps, cores = [], [], 0, 1
     for i in range(args.steps):
-        r = oracle_rate(scene, req, per_step, seed=i)
+        r = oracle_rate(scene, req, per_step, seed=i, rate_hint=rate)
+        rate = r["cells_per_s"]
         rates.append(r["value"])
         secs.append(r["seconds"])
         vps += r["viewpoints"]
@@ -244,26 +296,111 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(scene, req):
-    n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
-    return {"workload": WORKLOAD, "viewpoints": n_vp, "grid": [req["grid_nx"], req["grid_ny"]],
-            "layers_m": [z / 1024 for z in req["layer_z"]], "patches": [req["patches_u"], req["patches_w"]],
-            "boxes": scene.n, "scene_digest": scene.digest(), "color_levels": req["color_levels"],
-            "segments_per_step": n_vp * req["patches_u"] * req["patches_w"],
-            "l2": "512 MB buffer written between timed steps", "parallelism": "replicas"}
-
-
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def _device_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u[4:] if u.startswith("GPU-") else u
+    except Exception:
+        return None
+
+
+def time_direct(ctx, req, steps, warmup, stream, flush, sampler, what, preload_s=0.6, pg=None):
+    """Time `steps` direct calls (vcm_compute into device buffers) after
+    `warmup` untimed ones; L2 flushed before every call.  The same call also
+    runs untimed for about `preload_s` just before the timed region, so that
+    the clock samples (every 200 ms) cover that load; the clock window spans
+    both.  Returns per-step and per-k_tiles times (CUDA events on the launch
+    stream), the device counters and the output tensors."""
+    import torch
+
+    from paper_1310_7297_gb300 import n_viewpoints, stats_from_tensor
+    from paper_1310_7297_gb300.vcm import STATS_BYTES
+
+    dev = torch.device("cuda", ctx.device)
+    n_vp = n_viewpoints(req)
+    v = torch.empty(n_vp, dtype=torch.float32, device=dev)
+    col = torch.empty(n_vp, dtype=torch.uint8, device=dev)
+    st = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.vcm_compute(req, v.data_ptr(), col.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    t_load = time.monotonic()
+    while time.monotonic() - t_load < preload_s:
+        for _ in range(4):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    kb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ka = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for e in kb + ka:
+        e.record(stream)   # torch creates the CUDA event on first record; the library re-records it
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        ctx.vcm_set_timing_events(kb[i], ka[i])
+        s_ev[i].record(stream)
+        step()
+        e_ev[i].record(stream)
+    torch.cuda.synchronize()
+    t_end = time.monotonic()
+    ctx.vcm_set_timing_events(None, None)
+    return {"step_ms": [s.elapsed_time(e) for s, e in zip(s_ev, e_ev)],
+            "kern_ms": [b.elapsed_time(a) for b, a in zip(kb, ka)],
+            "stats": stats_from_tensor(st), "v": v, "color": col,
+            "clocks": sampler.window(t_load, t_end, what) if sampler else None}
+
+
+def alu_roofline(stats, dims, kern_ms, sm_count, profile=None):
+    """ALU roofline of k_tiles (both passes): the device-counted slab tests
+    x their algorithmic operations over the passes' CUDA-event time."""
+    max_mhz = float(peaks().get("sm_max_mhz", 2070.0))
+    peak = alu_peak_ops(sm_count, max_mhz)
+    kern_s = float(np.mean(kern_ms)) / 1e3
+    units = stats["slab_tests"] + stats["corner_tests"]
+    achieved = units * OPS_PER_SLAB_TEST[dims] / kern_s
+    issued = (stats["slab_tests"] * ISSUED_OPS_PER_ROW_TEST + stats["corner_tests"] * ISSUED_OPS_PER_CORNER_TEST) / kern_s
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": profiled_traffic(profile) if profile else None,
+            "kernel": "k_tiles (both passes)", "work_unit": "segment/box slab test",
+            "ops_per_unit": OPS_PER_SLAB_TEST[dims],
+            "issued_slab_ops": {"value": issued / 1e12, "frac": issued / peak,
+                                "ops_per_row_test": ISSUED_OPS_PER_ROW_TEST,
+                                "ops_per_corner_test": ISSUED_OPS_PER_CORNER_TEST},
+            "units_per_launch": units, "kernel_ms": float(np.mean(kern_ms)),
+            "peak_basis": "%d SMs x 128 lane-instr/clk x %.0f MHz (issue limit; derived, "
+                          "MEASURED_PEAKS.json has no ALU figure)" % (sm_count, max_mhz)}
+
+
+def executed(stats, v, ms):
+    """What the device actually did, beside the nominal segment rate."""
+    s = ms / 1e3
+    return {"nonzero_cells": int((v > 0).sum().item()), "slab_tests": stats["slab_tests"],
+            "corner_tests": stats["corner_tests"], "slab_tests_per_s": stats["slab_tests"] / s,
+            "corner_tests_per_s": stats["corner_tests"] / s,
+            "shortcut_viewpoints": stats["shortcut_viewpoints"], "shared_viewpoints": stats["shared_viewpoints"],
+            "rechecked": stats["rechecked"], "boxes_listed": stats["boxes_listed"],
+            "edge_cells": stats["edge_cells"], "v_ref": stats["v_ref"]}
+
+
 def run_gpu(args):
     import torch
 
-    import synth
-    from paper_1310_7297_gb300 import Context, stats_from_tensor
+    from paper_1310_7297_gb300 import Context
     from paper_1310_7297_gb300 import build as B
-    from paper_1310_7297_gb300.vcm import STATS_BYTES
+    from paper_1310_7297_gb300.vcm import STATS_BYTES, vcm_request
 
     world, rank, local = dist_setup()
     B.build()
@@ -275,73 +412,24 @@ def run_gpu(args):
 
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    scene, req = synth.workload_3d()
+    scene, req = headline_workload()
     n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
     P = req["patches_u"] * req["patches_w"]
     seg = n_vp * P
     ctx = Context(local)
     ctx.load_scene(scene)
-    ctx.vcm_build(0.0)
+    ctx.vcm_build(GRID_CELL_LARGE_M)
     stream = torch.cuda.current_stream(dev)
-    v = torch.empty(n_vp, dtype=torch.float32, device=dev)
-    col = torch.empty(n_vp, dtype=torch.uint8, device=dev)
-    st = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def step():
-        ctx.vcm_compute(req, v.data_ptr(), col.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    uuid = None
-    try:
-        u = str(torch.cuda.get_device_properties(dev).uuid)
-        uuid = u[4:] if u.startswith("GPU-") else u
-    except Exception:
-        pass
-    sampler = ClockSampler(uuid)
-    sampler.start()
+    sampler = ClockSampler(_device_uuid(torch, dev)).start()
     time.sleep(0.3)
-    # The timed region of a few ms is shorter than the 200 ms sampling
-    # period, so the same step also runs untimed for about half a second
-    # right before it; the clock summary covers that load and the timed
-    # region.
-    t_load = time.monotonic()
-    while time.monotonic() - t_load < 0.6:
-        for _ in range(20):
-            flush.zero_()
-            step()
-        torch.cuda.synchronize()
     K = args.steps
-    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    kb = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ka = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    for e in kb + ka:
-        e.record(stream)   # torch creates the CUDA event on first record; the library re-records it
-    torch.cuda.synchronize()
-    for i in range(K):
-        flush.zero_()
-        ctx.vcm_set_timing_events(kb[i], ka[i])
-        s_ev[i].record(stream)
-        step()
-        e_ev[i].record(stream)
-    torch.cuda.synchronize()
-    t_end = time.monotonic()
-    ctx.vcm_set_timing_events(None, None)
-    clocks = sampler.stop(t_load, t_end)
-    if clocks is not None:
-        clocks["window"] = "%.2f s: the same step untimed, then the timed region" % (t_end - t_load)
-    step_ms = [s.elapsed_time(e) for s, e in zip(s_ev, e_ev)]
-    kern_ms = [b.elapsed_time(a) for b, a in zip(kb, ka)]
-    total_ms = reduce_max(float(sum(step_ms)), pg, dev)
+    head = time_direct(ctx, req, K, args.warmup, stream, flush, sampler,
+                       "the same step untimed, then the timed region", pg=pg)
+    total_ms = reduce_max(float(sum(head["step_ms"])), pg, dev)
     if pg:
         pg.barrier()
-    stats = stats_from_tensor(st)
+    stats = head["stats"]
 
     # End to end through the public API with host buffers.  Headline: the
     # scene is a resident database (uploaded and indexed once, as the
@@ -357,7 +445,7 @@ def run_gpu(args):
             t0 = time.perf_counter()
             if with_scene:
                 ctx.vcm_scene_load_mem(lo, hi, 3)
-                ctx.vcm_build(0.0)
+                ctx.vcm_build(GRID_CELL_LARGE_M)
             t = ctx.vcm_submit(req)
             ctx.vcm_poll(t, -1)
             hv, hc, _, _ = ctx.vcm_result_get(t, copy=False)
@@ -367,10 +455,18 @@ def run_gpu(args):
                 ms.append(1e3 * (time.perf_counter() - t0))
         return ms
 
+    t_e2e = time.monotonic()
     e2e_scene_ms = e2e_loop(True)
     e2e_ms = e2e_loop(False)
+    e2e_clocks = sampler.window(t_e2e, time.monotonic(), "both end-to-end loops")
     e2e_scene_total = reduce_max(float(sum(e2e_scene_ms)), pg, dev)
     e2e_total = reduce_max(float(sum(e2e_ms)), pg, dev)
+
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras["config_3d_5000_boxes"] = sub_3d(ctx, args, stream, flush, sampler)
+        extras["batched"] = sub_batched(ctx, args, stream, sampler)
+        extras["serve"] = sub_serve(ctx, args, sampler)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -378,23 +474,14 @@ def run_gpu(args):
         cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                "sample": "%d random viewpoints of the workload (%d patches each), %.1f s of CPU work"
                          % (r["viewpoints"], P, r["seconds"])}
+    sampler.stop()
 
     # the request as uploaded: its descriptor and the coordinates the library
     # derives from it (patch centres, viewpoint x, y, layer heights)
-    from paper_1310_7297_gb300.vcm import vcm_request
     req_bytes = int(ctypes.sizeof(vcm_request) + 4 * (req["patches_u"] + req["patches_w"] + req["grid_nx"] +
                                                        req["grid_ny"] + len(req["layer_z"])))
     if rank == 0:
-        pk = peaks()
-        props = torch.cuda.get_device_properties(dev)
-        sm_count = props.multi_processor_count
-        max_mhz = float(pk.get("sm_max_mhz", 2070.0))
-        peak = alu_peak_ops(sm_count, max_mhz)
-        kern_avg_s = float(np.mean(kern_ms)) / 1e3
-        units = stats["slab_tests"] + stats["corner_tests"]
-        achieved = units * OPS_PER_SLAB_TEST[req["dims"]] / kern_avg_s
-        issued = (stats["slab_tests"] * ISSUED_OPS_PER_ROW_TEST +
-                  stats["corner_tests"] * ISSUED_OPS_PER_CORNER_TEST) / kern_avg_s
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
         value = world * seg * K / (total_ms / 1e3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -402,39 +489,51 @@ def run_gpu(args):
             "dtype": "f32", "data": "synthetic",
             "config": config_dict(scene, req),
             "cells_per_s": world * n_vp * K / (total_ms / 1e3),
-            "kernel_ms": float(np.mean(kern_ms)),
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(),
-                         "kernel": "k_tiles", "work_unit": "segment/box slab test",
-                         "ops_per_unit": OPS_PER_SLAB_TEST[req["dims"]],
-                         "issued_slab_ops": {"value": issued / 1e12, "frac": issued / peak,
-                                             "ops_per_row_test": ISSUED_OPS_PER_ROW_TEST,
-                                             "ops_per_corner_test": ISSUED_OPS_PER_CORNER_TEST},
-                         "units_per_launch": units,
-                         "peak_basis": "%d SMs x 128 lane-instr/clk x %.0f MHz (issue limit)" % (sm_count, max_mhz)},
-            "stats": {"slab_tests": stats["slab_tests"], "corner_tests": stats["corner_tests"],
-                      "shortcut_viewpoints": stats["shortcut_viewpoints"], "rechecked": stats["rechecked"],
-                      "shared_viewpoints": stats["shared_viewpoints"],
-                      "boxes_listed": stats["boxes_listed"], "edge_cells": stats["edge_cells"],
-                      "v_ref": stats["v_ref"], "nonzero_cells": int((v > 0).sum().item())},
+            "kernel_ms": float(np.mean(head["kern_ms"])),
+            "roofline": alu_roofline(stats, req["dims"], head["kern_ms"], sm_count, PROFILE_LARGE),
+            "executed": executed(stats, head["v"], total_ms / K),
             "cpu_baseline": cpu,
             "e2e": {"value": world * seg * K / (e2e_total / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": req_bytes, "d2h_bytes_per_step": int(n_vp * 5 + STATS_BYTES),
                     "ms_per_step": e2e_total / K,
                     "path": "vcm_submit, vcm_poll, vcm_result_get (values and colours into pinned host memory); "
-                            "scene resident, uploaded and indexed once"},
+                            "scene resident, uploaded and indexed once",
+                    "clocks": e2e_clocks},
             "e2e_scene_per_step": {"value": world * seg * K / (e2e_scene_total / 1e3), "unit": UNIT,
                                    "h2d_bytes_per_step": int(lo.nbytes + hi.nbytes) + req_bytes,
                                    "d2h_bytes_per_step": int(n_vp * 5 + STATS_BYTES),
                                    "ms_per_step": e2e_scene_total / K,
                                    "path": "vcm_scene_load_mem and vcm_build every step, then as e2e"},
             "gpu_launches": LAUNCHES_PER_STEP * K,
-            "clocks": clocks,
+            "clocks": head["clocks"],
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     ctx.close()
     if pg:
         pg.destroy_process_group()
+
+
+def sub_3d(ctx, args, stream, flush, sampler):
+    """The 3D workload of 5,000 boxes (512 x 512 x 5 viewpoints, 32 x 16
+    patches), timed like the headline."""
+    import torch
+
+    import synth
+
+    scene, req = synth.workload_3d()
+    ctx.load_scene(scene)
+    ctx.vcm_build(0.0)
+    n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
+    seg = n_vp * req["patches_u"] * req["patches_w"]
+    r = time_direct(ctx, req, args.steps, args.warmup, stream, flush, sampler,
+                    "the same step untimed, then the timed region")
+    ms = float(np.mean(r["step_ms"]))
+    sm_count = torch.cuda.get_device_properties(stream.device).multi_processor_count
+    return {"workload": WORKLOAD_3D, "boxes": scene.n, "scene_digest": scene.digest(), "value": seg / (ms / 1e3),
+            "unit": UNIT, "ms_per_step": ms, "cells_per_s": n_vp / (ms / 1e3),
+            "roofline": alu_roofline(r["stats"], 3, r["kern_ms"], sm_count, PROFILE_3D),
+            "executed": executed(r["stats"], r["v"], ms), "clocks": r["clocks"]}
 
 
 # ---------------------------------------------------------------------------
@@ -451,26 +550,25 @@ def _alloc_outputs(torch, dev, reqs):
     return vs, cs, st
 
 
-def run_batched(args):
-    """256 uneven requests over a shared 50,000-box scene: one persistent
-    launch (default shapes, then autotuned shapes) against one launch per
-    request (autotuned shapes)."""
+def sub_batched(ctx, args, stream, sampler, autotune=False):
+    """The 256-request uneven mix over a shared 50,000-box scene: one
+    persistent launch (default shapes; with autotune also the tuned shapes)
+    against one launch per request, each timed with CUDA events on the
+    launch stream; the persistent launch's ALU roofline from the device
+    counters over the tile kernel's event time."""
     import torch
 
     import synth
-    from paper_1310_7297_gb300 import Context, n_viewpoints
-    from paper_1310_7297_gb300 import build as B
+    from paper_1310_7297_gb300 import n_viewpoints, stats_from_tensor
     from paper_1310_7297_gb300.vcm import STATS_BYTES
 
-    B.build()
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", ctx.device)
     scene, reqs = synth.workload_batched(n_requests=args.batch_requests)
     seg = sum(n_viewpoints(r) * r["patches_u"] * r["patches_w"] for r in reqs)
-    ctx = Context(0)
     ctx.load_scene(scene)
     ctx.vcm_build(50.0)
     vs, cs, st = _alloc_outputs(torch, dev, reqs)
-    stream = torch.cuda.current_stream(dev)
+    steps = max(1, min(args.steps, 10))
 
     def batch():
         ctx.vcm_compute_batch(reqs, [t.data_ptr() for t in vs], [t.data_ptr() for t in cs], [None] * len(reqs),
@@ -478,51 +576,64 @@ def run_batched(args):
 
     def singles():
         for i, r in enumerate(reqs):
-            ctx.vcm_compute(r, vs[i].data_ptr(), cs[i].data_ptr(), None, st.data_ptr() + STATS_BYTES * i, stream.cuda_stream)
+            ctx.vcm_compute(r, vs[i].data_ptr(), cs[i].data_ptr(), None, st.data_ptr() + STATS_BYTES * i,
+                            stream.cuda_stream)
 
-    def timed(fn):
+    def timed(fn, what):
         for _ in range(max(1, args.warmup)):
             fn()
         torch.cuda.synchronize()
-        ms = []
-        for _ in range(args.steps):
+        t0 = time.monotonic()
+        ms, kern = [], []
+        kb, ka = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kb.record(stream)
+        ka.record(stream)
+        torch.cuda.synchronize()
+        for _ in range(steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ctx.vcm_set_timing_events(kb, ka)
             a.record(stream)
             fn()
             b.record(stream)
             torch.cuda.synchronize()
+            ctx.vcm_set_timing_events(None, None)
             ms.append(a.elapsed_time(b))
-        return {"ms": float(np.median(ms)), "segments_per_s": seg / (float(np.median(ms)) / 1e3)}
+            kern.append(kb.elapsed_time(ka))
+        m = float(np.median(ms))
+        return {"ms": m, "segments_per_s": seg / (m / 1e3), "steps": steps, "kern_ms": kern,
+                "clocks": sampler.window(t0, time.monotonic(), what) if sampler else None}
 
-    res = {"persistent_batch_default_shapes": timed(batch)}
-    t0 = time.perf_counter()
-    # 16 requests of the mix (a seeded sample) stand for it
-    pick = np.random.default_rng(7).choice(len(reqs), size=min(16, len(reqs)), replace=False)
-    samples = [reqs[i] for i in sorted(pick)]
-    tuned = ctx.vcm_autotune(samples)
-    tune_s = time.perf_counter() - t0
-    res["persistent_batch"] = timed(batch)
-    # roofline of the batched launch: slab-test operations counted on the
-    # device over the batch's time (which also holds the small prologue and
-    # colour kernels, so the fraction is a lower bound)
-    from paper_1310_7297_gb300 import stats_from_tensor
+    res = {"workload": "256 uneven requests (2-50 m targets, 64^2-1024^2 x 1-8 layer grids, 8x4-64x32 patches) "
+                       "over a shared 50,000-box scene", "requests": len(reqs), "boxes": scene.n, "segments": seg,
+           "unit": UNIT}
+    res["persistent_batch"] = timed(batch, "the persistent batch, timed")
+    if autotune:
+        t0 = time.perf_counter()
+        pick = np.random.default_rng(7).choice(len(reqs), size=min(16, len(reqs)), replace=False)
+        tuned = ctx.vcm_autotune([reqs[i] for i in sorted(pick)])
+        res["autotune_s"] = time.perf_counter() - t0
+        res["tuned_shapes"] = sorted(set(map(tuple, tuned)))
+        res["persistent_batch_tuned"] = timed(batch, "the persistent batch with tuned shapes, timed")
     batch()
     torch.cuda.synchronize()
     per = [stats_from_tensor(st[i * STATS_BYTES:(i + 1) * STATS_BYTES]) for i in range(len(reqs))]
-    ops = sum((p["slab_tests"] + p["corner_tests"]) * OPS_PER_SLAB_TEST[r["dims"]] for p, r in zip(per, reqs))
-    props = torch.cuda.get_device_properties(dev)
-    peak = alu_peak_ops(props.multi_processor_count, float(peaks().get("sm_max_mhz", 2070.0)))
-    achieved = ops / (res["persistent_batch"]["ms"] / 1e3)
-    res["persistent_batch"]["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                                           "unit": "Tops/s", "frac": achieved / peak}
-    res["one_per_launch"] = timed(singles)
-    print(json.dumps({"mode": "batched", "metric": METRIC, "unit": UNIT, "requests": len(reqs), "boxes": scene.n,
-                      "segments": seg, "autotune_s": tune_s, "tuned_shapes": sorted(set(map(tuple, tuned))),
-                      **res, "speedup": res["one_per_launch"]["ms"] / res["persistent_batch"]["ms"]}), flush=True)
-    ctx.close()
+    tot = {k: sum(p[k] for p in per) for k in ("slab_tests", "corner_tests", "shortcut_viewpoints",
+                                               "shared_viewpoints", "rechecked")}
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    pb = res["persistent_batch"]
+    pb["roofline"] = alu_roofline(tot, 3, pb.pop("kern_ms"), sm_count)
+    pb["executed"] = {k: tot[k] for k in tot}
+    pb["executed"]["nonzero_cells"] = int(sum(int((t > 0).sum().item()) for t in vs))
+    if "persistent_batch_tuned" in res:
+        res["persistent_batch_tuned"].pop("kern_ms")
+    res["one_per_launch"] = timed(singles, "one launch per request, timed")
+    res["one_per_launch"].pop("kern_ms")
+    res["speedup"] = res["one_per_launch"]["ms"] / res["persistent_batch"]["ms"]
+    del vs, cs, st
+    return res
 
 
-def run_serve(args):
+def sub_serve(ctx, args, sampler):
     """Poisson arrivals of requests from the batched mix against a resident
     100,000-box scene.  Continuous batching (vcm_submit / vcm_poll: queued
     requests are admitted into slots as memory and slots free up, and run as
@@ -535,14 +646,11 @@ def run_serve(args):
     import torch
 
     import synth
-    from paper_1310_7297_gb300 import Context, n_viewpoints
-    from paper_1310_7297_gb300 import build as B
+    from paper_1310_7297_gb300 import n_viewpoints
     from paper_1310_7297_gb300.vcm import STATS_BYTES
 
-    B.build()
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", ctx.device)
     scene, _ = synth.workload_3d_large(grid=64, layers=1)
-    ctx = Context(0, 64 << 30)
     ctx.load_scene(scene)
     ctx.vcm_build(50.0)
     ctx.vcm_set_slots(args.slots, args.max_batch)
@@ -564,13 +672,18 @@ def run_serve(args):
             h_c[:n].copy_(d_c[:n], non_blocking=True)
         stream.synchronize()
 
-    for r in pool[:8]:
+    for r in pool:
         fifo_one(r)
-    # warm the scheduler path too
-    for t in [ctx.vcm_submit(r) for r in pool[:8]]:
+    # warm the scheduler path too: every request once, alone and in a burst
+    for r in pool[:16]:
+        t = ctx.vcm_submit(r)
+        ctx.vcm_poll(t, -1)
+        ctx.vcm_result_release(t)
+    for t in [ctx.vcm_submit(r) for r in pool]:
         ctx.vcm_poll(t, -1)
         ctx.vcm_result_release(t)
     out = []
+    t_start = time.monotonic()
     for rate in args.rates:
         n = int(min(args.serve_count, max(40, rate * args.serve_seconds)))
         arr = synth.poisson_arrivals(int(rate), float(rate), n)
@@ -588,6 +701,7 @@ def run_serve(args):
                 done[i] = time.perf_counter() - t0
 
         th = threading.Thread(target=worker)
+        t_w = time.monotonic()
         th.start()
         t0 = time.perf_counter()
         for i in range(n):
@@ -598,10 +712,11 @@ def run_serve(args):
         th.join()
         lat = [1e3 * (done[i] - arr[i]) for i in range(n)]
         fifo = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "segments_per_s": seg / max(done)}
+                "segments_per_s": seg / max(done), "clocks": sampler.window(t_w, time.monotonic(), "FIFO arm")}
 
         # continuous batching through the scheduler
         tickets = [None] * n
+        t_w = time.monotonic()
         t0 = time.perf_counter()
         for i in range(n):
             now = time.perf_counter() - t0
@@ -617,61 +732,55 @@ def run_serve(args):
             last = max(last, arr[i] + lat2[-1] / 1e3)
             ctx.vcm_result_release(t)
         cont = {"p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
-                "segments_per_s": seg / last}
+                "segments_per_s": seg / last, "clocks": sampler.window(t_w, time.monotonic(), "continuous arm")}
         out.append({"rate_per_s": rate, "requests": n, "continuous": cont, "one_per_launch_fifo": fifo})
-    print(json.dumps({"mode": "serve", "metric": METRIC, "unit": UNIT, "boxes": scene.n, "budget_gb": 64,
-                      "slots": args.slots, "max_batch": args.max_batch, "rates": out}), flush=True)
-    ctx.close()
+    ctx.vcm_set_slots(4, 64)
+    return {"workload": "Poisson arrivals of requests from the batched mix against a resident 100,000-box scene",
+            "unit": UNIT, "boxes": scene.n, "budget_gb": 64, "slots": args.slots, "max_batch": args.max_batch,
+            "rates": out, "clocks": sampler.window(t_start, time.monotonic(), "all rates, both arms")}
 
 
-def run_large(args):
-    """The large scene at full size: 100,000 boxes over 10 km x 10 km, one
-    40 m x 20 m target split 64 x 32, 2048 x 2048 x 8 viewpoints, 50 m grid
-    index.  Same timing rules as the default step."""
+def _standalone(args, fn, **kw):
+    """Run one sub-record on its own (a --mode) with its own context."""
     import torch
 
-    import synth
-    from paper_1310_7297_gb300 import Context, stats_from_tensor
+    from paper_1310_7297_gb300 import Context
     from paper_1310_7297_gb300 import build as B
-    from paper_1310_7297_gb300.vcm import STATS_BYTES
 
     B.build()
     dev = torch.device("cuda", 0)
-    scene, req = synth.workload_3d_large()
-    n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
-    seg = n_vp * req["patches_u"] * req["patches_w"]
-    ctx = Context(0)
-    ctx.load_scene(scene)
-    ctx.vcm_build(50.0)
-    stream = torch.cuda.current_stream(dev)
-    v = torch.empty(n_vp, dtype=torch.float32, device=dev)
-    c = torch.empty(n_vp, dtype=torch.uint8, device=dev)
-    st = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    for _ in range(max(1, args.warmup)):
-        ctx.vcm_compute(req, v.data_ptr(), c.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
-    ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ctx.vcm_compute(req, v.data_ptr(), c.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
-    stats = stats_from_tensor(st)
-    out = {"mode": "large", "metric": METRIC, "unit": UNIT, "boxes": scene.n, "viewpoints": n_vp,
-           "patches": [req["patches_u"], req["patches_w"]], "segments": seg, "ms_per_step": float(np.mean(ms)),
-           "value": seg / (float(np.mean(ms)) / 1e3), "cells_per_s": n_vp / (float(np.mean(ms)) / 1e3),
-           "stats": {k: stats[k] for k in ("slab_tests", "corner_tests", "shortcut_viewpoints", "rechecked",
-                                           "boxes_listed")},
-           "nonzero_cells": int((v > 0).sum().item())}
-    if not args.no_cpu_baseline:
-        r = oracle_rate(scene, req, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                               "sample": "%d random viewpoints, %.1f s" % (r["viewpoints"], r["seconds"])}
-    print(json.dumps(out), flush=True)
-    ctx.close()
+    sampler = ClockSampler(_device_uuid(torch, dev)).start()
+    time.sleep(0.3)
+    ctx = Context(0, 64 << 30)
+    try:
+        return fn(ctx, args, sampler=sampler, **kw)
+    finally:
+        sampler.stop()
+        ctx.close()
+
+
+def run_batched(args):
+    import torch
+
+    out = _standalone(args, lambda ctx, a, sampler: sub_batched(ctx, a, torch.cuda.current_stream(), sampler,
+                                                                autotune=True))
+    print(json.dumps(dict(mode="batched", metric=METRIC, **out)), flush=True)
+
+
+def run_serve(args):
+    out = _standalone(args, sub_serve)
+    print(json.dumps(dict(mode="serve", metric=METRIC, **out)), flush=True)
+
+
+def run_step3d(args):
+    import torch
+
+    def fn(ctx, a, sampler):
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        return sub_3d(ctx, a, torch.cuda.current_stream(), flush, sampler)
+
+    out = _standalone(args, fn)
+    print(json.dumps(dict(mode="step3d", metric=METRIC, **out)), flush=True)
 
 
 def run_gaze(args):
@@ -696,6 +805,7 @@ def run_gaze(args):
     n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
     P = req["patches_u"] * req["patches_w"]
     words = (P + 31) // 32
+    sampler = ClockSampler(_device_uuid(torch, dev)).start()
     ctx = Context(0)
     ctx.load_scene(scene)
     ctx.vcm_build(0.0)
@@ -718,6 +828,7 @@ def run_gaze(args):
     for e in kb + ka:
         e.record(stream)
     torch.cuda.synchronize()
+    t_w = time.monotonic()
     rec, kern, full = [], [], []
     for k in range(args.steps):
         r = gaze_req(k)
@@ -737,6 +848,8 @@ def run_gaze(args):
         b.record(stream)
         torch.cuda.synchronize()
         full.append(a.elapsed_time(b))
+    clocks = sampler.window(t_w, time.monotonic(), "recolours and full recomputes, alternating")
+    sampler.stop()
     k_ms = float(np.mean(kern))
     # words are read for the viewpoints in front of the one-sided target only
     # (the target faces req["normal"]); one float is written per viewpoint
@@ -757,7 +870,7 @@ def run_gaze(args):
                         "unit": "GB/s", "frac": achieved / peak["value"], "peak_basis": peak["basis"],
                         "bytes_per_launch": bytes_per_launch, "front_viewpoints": n_front, "kernel_ms": k_ms,
                         "traffic": None},
-           "l2": "512 MB buffer written between timed calls"}
+           "l2": "512 MB buffer written between timed calls", "clocks": clocks}
     print(json.dumps(out), flush=True)
     ctx.close()
 
@@ -791,65 +904,84 @@ def run_modes(args):
     import torch
 
     import synth
-    from paper_1310_7297_gb300 import VCM_VIEWER, Context, stats_from_tensor
+    from paper_1310_7297_gb300 import VCM_VIEWER, Context
     from paper_1310_7297_gb300 import build as B
-    from paper_1310_7297_gb300.vcm import STATS_BYTES
 
     B.build()
     dev = torch.device("cuda", 0)
     scene, req = synth.workload_3d()
     n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
     variants = mode_variants(req)
+    sampler = ClockSampler(_device_uuid(torch, dev)).start()
     ctx = Context(0)
     ctx.load_scene(scene)
     ctx.vcm_build(0.0)
     stream = torch.cuda.current_stream(dev)
-    v = torch.empty(n_vp, dtype=torch.float32, device=dev)
-    c = torch.empty(n_vp, dtype=torch.uint8, device=dev)
-    st = torch.empty(STATS_BYTES, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    pk = peaks()
-    max_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak = alu_peak_ops(torch.cuda.get_device_properties(dev).multi_processor_count, max_mhz)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     results = []
     for name, r in variants:
         P = 1 if r.get("flags", 0) & VCM_VIEWER else r["patches_u"] * r["patches_w"]
-        for _ in range(max(3, args.warmup)):
-            ctx.vcm_compute(r, v.data_ptr(), c.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
-        torch.cuda.synchronize()
-        kb, ka = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        kb.record(stream)   # torch creates an event's handle on its first record
-        ka.record(stream)
-        torch.cuda.synchronize()
-        step, kern = [], []
-        for _ in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ctx.vcm_set_timing_events(kb, ka)
-            a.record(stream)
-            ctx.vcm_compute(r, v.data_ptr(), c.data_ptr(), None, st.data_ptr(), stream.cuda_stream)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ctx.vcm_set_timing_events(None, None)
-            step.append(a.elapsed_time(b))
-            kern.append(kb.elapsed_time(ka))
-        stats = stats_from_tensor(st)
-        ms, k_ms = float(np.mean(step)), float(np.mean(kern))
-        ops = (stats["slab_tests"] + stats["corner_tests"]) * OPS_PER_SLAB_TEST[r["dims"]]
-        row = {"name": name, "flags": int(r.get("flags", 0)), "ms_per_step": ms, "kernel_ms": k_ms,
+        t = time_direct(ctx, r, args.steps, max(3, args.warmup), stream, flush, sampler,
+                        "the variant untimed, then timed", preload_s=0.4)
+        ms, stats = float(np.mean(t["step_ms"])), t["stats"]
+        row = {"name": name, "flags": int(r.get("flags", 0)), "ms_per_step": ms,
+               "kernel_ms": float(np.mean(t["kern_ms"])),
                "segments_per_s": n_vp * P / (ms / 1e3), "cells_per_s": n_vp / (ms / 1e3),
-               "nonzero_cells": int((v > 0).sum().item()),
-               "roofline": {"bound": "alu", "achieved": ops / (k_ms / 1e3) / 1e12, "peak": peak / 1e12,
-                            "unit": "Tops/s", "frac": ops / (k_ms / 1e3) / peak}}
+               "nonzero_cells": int((t["v"] > 0).sum().item()),
+               "roofline": alu_roofline(stats, r["dims"], t["kern_ms"], sm_count), "clocks": t["clocks"]}
         if not args.no_cpu_baseline:
             o = oracle_rate(scene, r, max(1.0, args.cpu_seconds / len(variants)), seed=len(results))
             row["cpu_oracle"] = {"segments_per_s": o["cells_per_s"] * P, "cells_per_s": o["cells_per_s"],
                                  "cores": o["cores"], "sample": "%d random viewpoints, %.1f s" % (o["viewpoints"],
                                                                                                o["seconds"])}
         results.append(row)
-    print(json.dumps({"mode": "modes", "workload": WORKLOAD, "steps": args.steps,
+    sampler.stop()
+    print(json.dumps({"mode": "modes", "workload": WORKLOAD_3D, "steps": args.steps,
                       "l2": "512 MB buffer written between timed steps", "results": results}), flush=True)
     ctx.close()
+
+
+EQUIVISIBLE_WORKLOAD = "2D, 10 m target, 1024 x 1024 cells over 1 km, no obstacles, 16 levels"
+
+
+def equivisible_dense(ctx, S=10.0, n=1024, half=500.0, levels=16, samples=64):
+    """The dense GPU map of a 2D segment target of length S at the origin
+    facing +y over an n x n grid of 2 half metres a side, no obstacles.
+    Returns (request, device v, colours, cell-centre x, y as numpy)."""
+    import synth
+
+    scene = synth.Scene(2, np.zeros((0, 3), np.int64), np.zeros((0, 3), np.int64))
+    req = synth.make_request(2, (0.0, 0.0), synth.AXIS_PX, synth.AXIS_PY, S, samples, (-half, -half),
+                             (2 * half / n, 2 * half / n), (n, n), color_levels=levels)
+    ctx.load_scene(scene)
+    ctx.vcm_build(0.0)
+    v, c, _, _ = ctx.compute(req)
+    xs = -half + (np.arange(n) + 0.5) * (2 * half / n)
+    X, Y = np.meshgrid(xs, xs)
+    return req, v, c.cpu().numpy().astype(np.int64), X.ravel(), Y.ravel()
+
+
+def equivisible_row(c_dense, X, Y, mu, S=10.0, levels=16, d0=1.0):
+    """Eq. 6 errors of the paper's partition at angular resolution mu against
+    the dense map, with the paper's own measure (Eq. 1 with Eq. 2's
+    perceived size) and with the dense map's measure (the exact subtended
+    angle), over the grid and within the partition's range d_max."""
+    from paper_1310_7297_gb300 import equivisible as E
+
+    t1 = time.perf_counter()
+    P = E.Partition(S, mu, d0)
+    vp = P.values_at(X, Y)
+    cpu_s = time.perf_counter() - t1
+    c_paper = E.quantise(vp, levels)
+    c_same = E.quantise(P.values_at(X, Y, lambda D, a: E.subtended(S, D, a)), levels)
+    inside = np.hypot(X, Y) < P.d_edges[-1]
+    return {"mu_deg": mu, "cells": P.n_cells(), "d_max_m": float(P.d_edges[-1]), "cpu_s": cpu_s,
+            "eq6_paper_measure": E.eq6_error(c_dense, c_paper),
+            "eq6_paper_measure_within_d_max": E.eq6_error(c_dense[inside], c_paper[inside]),
+            "eq6_same_measure": E.eq6_error(c_dense, c_same),
+            "eq6_same_measure_within_d_max": E.eq6_error(c_dense[inside], c_same[inside]),
+            "mean_abs_colour_diff_within_d_max": float(np.mean(np.abs(c_dense[inside] - c_same[inside])))}
 
 
 def run_equivisible(args):
@@ -862,52 +994,18 @@ def run_equivisible(args):
     maximum; the near point is 1 m."""
     import torch
 
-    import synth
     from paper_1310_7297_gb300 import Context
     from paper_1310_7297_gb300 import build as B
-    from paper_1310_7297_gb300 import equivisible as E
 
     B.build()
-    S, n, half, levels = 10.0, 1024, 500.0, 16
-    scene = synth.Scene(2, np.zeros((0, 3), np.int64), np.zeros((0, 3), np.int64))
-    req = synth.make_request(2, (0.0, 0.0), synth.AXIS_PX, synth.AXIS_PY, S, 64, (-half, -half),
-                             (2 * half / n, 2 * half / n), (n, n), color_levels=levels)
     ctx = Context(0)
-    ctx.load_scene(scene)
-    ctx.vcm_build(0.0)
     t0 = time.perf_counter()
-    v, c, _, _ = ctx.compute(req)
+    _, _, c_dense, X, Y = equivisible_dense(ctx)
     torch.cuda.synchronize()
     gpu_ms = 1e3 * (time.perf_counter() - t0)
-    c_dense = c.cpu().numpy().astype(np.int64)
-    xs = -half + (np.arange(n) + 0.5) * (2 * half / n)
-    X, Y = np.meshgrid(xs, xs)
-    X, Y = X.ravel(), Y.ravel()
-
-    def subtended(D, a_deg):
-        # exact angle subtended by the segment from a point at distance D and
-        # viewing angle a (the limit of the dense map's sum)
-        a = np.radians(a_deg)
-        px, py = D * np.cos(a), D * np.sin(a)
-        return np.abs(np.arctan2(py, px - S / 2) - np.arctan2(py, px + S / 2))
-
-    rows = []
-    for mu in (1, 2, 4, 8, 16):
-        t1 = time.perf_counter()
-        P = E.Partition(S, mu, 1.0)
-        vp = P.values_at(X, Y)
-        cpu_s = time.perf_counter() - t1
-        c_paper = E.quantise(vp, levels)
-        c_same = E.quantise(P.values_at(X, Y, subtended), levels)
-        inside = np.hypot(X, Y) < P.d_edges[-1]
-        rows.append({"mu_deg": mu, "cells": P.n_cells(), "d_max_m": float(P.d_edges[-1]), "cpu_s": cpu_s,
-                     "eq6_paper_measure": E.eq6_error(c_dense, c_paper),
-                     "eq6_paper_measure_within_d_max": E.eq6_error(c_dense[inside], c_paper[inside]),
-                     "eq6_same_measure": E.eq6_error(c_dense, c_same),
-                     "eq6_same_measure_within_d_max": E.eq6_error(c_dense[inside], c_same[inside]),
-                     "mean_abs_colour_diff_within_d_max": float(np.mean(np.abs(c_dense[inside] - c_same[inside])))})
-    print(json.dumps({"mode": "equivisible", "workload": "2D, 10 m target, 1024 x 1024 cells over 1 km, no "
-                      "obstacles, 16 levels", "dense_gpu_ms": gpu_ms, "rows": rows}), flush=True)
+    rows = [equivisible_row(c_dense, X, Y, mu) for mu in (1, 2, 4, 8, 16)]
+    print(json.dumps({"mode": "equivisible", "workload": EQUIVISIBLE_WORKLOAD, "dense_gpu_ms": gpu_ms,
+                      "rows": rows}), flush=True)
     ctx.close()
 
 
@@ -919,28 +1017,31 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "batched", "serve", "large", "gaze", "equivisible", "modes"],
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: skip the 5,000-box, batched and serving sub-records")
+    ap.add_argument("--mode", choices=["step", "step3d", "batched", "serve", "gaze", "equivisible", "modes"],
                     default="step",
-                    help="step: the timed VCM step (default); batched / serve: the batching and serving runs; "
-                         "large: the 100,000-box scene at full size; gaze: recolouring for new gazes; "
-                         "equivisible: the paper's equi-visible cells against the dense map (Eq. 6); "
-                         "modes: strict, field of view, two-sided and viewer-centric variants of the step")
+                    help="step: the headline line on the 100,000-box scene with the sub-records (default); "
+                         "step3d: the 5,000-box 3D step alone; batched / serve: the batching and serving runs "
+                         "alone (batched adds the autotuner); gaze: recolouring for new gazes; equivisible: the "
+                         "paper's equi-visible cells against the dense map (Eq. 6); modes: strict, field of view, "
+                         "two-sided and viewer-centric variants of the 3D step")
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=400)
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--rates", type=float, nargs="+", default=[50, 100, 200, 500, 1000, 2000])
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--max-batch", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "step3d":
+        run_step3d(args)
     elif args.mode == "batched":
         run_batched(args)
     elif args.mode == "serve":
         run_serve(args)
-    elif args.mode == "large":
-        run_large(args)
     elif args.mode == "gaze":
         run_gaze(args)
     elif args.mode == "equivisible":

@@ -141,3 +141,14 @@ def eq6_error(c_exact, c_approx, area=None):
     a = np.ones(c_exact.shape) if area is None else np.asarray(area, np.float64)
     den = float(np.sum(c_exact * a))
     return float(np.sum((c_exact - c_approx) * a)) / den if den > 0 else 0.0
+
+
+def subtended(S, D, alpha_deg):
+    """Angle (radians) subtended by a segment of length S centred at the
+    origin along x, from the point at distance D and viewing angle alpha
+    (degrees from the segment's line): the unobstructed limit of the dense
+    map's measure, sum of len cos(theta) / d, as the samples get finer."""
+    a = np.radians(np.asarray(alpha_deg, np.float64))
+    D = np.asarray(D, np.float64)
+    px, py = D * np.cos(a), D * np.sin(a)
+    return np.abs(np.arctan2(py, px - S / 2.0) - np.arctan2(py, px + S / 2.0))
