@@ -74,6 +74,10 @@ def lib():
         L.vo_run.argtypes = [ctypes.POINTER(VoScene), ctypes.POINTER(VoRequest), _i64p,
                              ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
+        L.vo_run_ex.argtypes = [ctypes.POINTER(VoScene), ctypes.POINTER(VoRequest), _i64p,
+                                ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.vo_fov_test.argtypes = [ctypes.POINTER(VoRequest), _i64p, _i64p, ctypes.POINTER(ctypes.c_double)]
         L.vo_max.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int64]
         L.vo_max.restype = ctypes.c_double
         L.vo_quantise.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
@@ -155,9 +159,12 @@ def default_threads():
     return max(1, os.cpu_count() or 1)
 
 
-def run(scene, req, indices=None, bits=False, threads=None):
+def run(scene, req, indices=None, bits=False, threads=None, band=False):
     """Visibility (float64) of the given viewpoint indices (all by default),
-    and optionally the occlusion bits as uint32 [n, ceil(P/32)]."""
+    and optionally the occlusion bits as uint32 [n, ceil(P/32)] and the
+    field-of-view band as float64 [n, 3] (pairs within the band of the
+    cone's edge, the terms of those counted, the terms of those left out).
+    Returns v, or a tuple (v, bits) / (v, band) / (v, bits, band)."""
     pk = _Pack(scene, req)
     nvp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
     if indices is None:
@@ -168,13 +175,26 @@ def run(scene, req, indices=None, bits=False, threads=None):
     words = (P + 31) // 32
     v = np.zeros(n, np.float64)
     b = np.zeros((n, words), np.uint32) if bits else None
-    rc = lib().vo_run(ctypes.byref(pk.s), ctypes.byref(pk.r), _p64(indices), n,
-                      v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                      b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)) if bits else None,
-                      int(threads or default_threads()))
+    bd = np.zeros((n, 3), np.float64) if band else None
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib().vo_run_ex(ctypes.byref(pk.s), ctypes.byref(pk.r), _p64(indices), n, v.ctypes.data_as(dp),
+                         b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)) if bits else None,
+                         bd.ctypes.data_as(dp) if band else None, int(threads or default_threads()))
     if rc != 0:
         raise ValueError("oracle rejected the request")
-    return (v, b) if bits else v
+    out = (v,) + ((b,) if bits else ()) + ((bd,) if band else ())
+    return out[0] if len(out) == 1 else out
+
+
+def fov_test(req, q, p):
+    """Cone decision for the pair (q, p) in units: (inside, relative margin),
+    or (None, 0.0) when the request has no cone."""
+    pk = _Pack(None, req)
+    qa = np.ascontiguousarray(list(q) + [0] * (3 - len(q)), dtype=np.int64)
+    pa = np.ascontiguousarray(list(p) + [0] * (3 - len(p)), dtype=np.int64)
+    m = ctypes.c_double(0.0)
+    r = lib().vo_fov_test(ctypes.byref(pk.r), _p64(qa), _p64(pa), ctypes.byref(m))
+    return (None, 0.0) if r < 0 else (bool(r), m.value)
 
 
 def vmax(v):

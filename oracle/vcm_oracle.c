@@ -202,41 +202,59 @@ static double viewer_value(const vo_scene *s, const vo_request *r, const int64_t
     return 4.0 * asin(S * S / (S * S + 4.0 * D * D));  /* S x S square facing the viewer */
 }
 
-/* Field of view (vcm_oracle.h): the cone's cosine c and unit axis a, or 0
- * when there is no cone. */
-static int fov_setup(const vo_request *r, float *c, float a[3])
+/* Field of view (vcm_oracle.h): the cosine c of the cone's half-angle and
+ * its unit axis a, in float64, or 0 when there is no cone. */
+static int fov_setup(const vo_request *r, double *c, double a[3])
 {
     if (!(r->fov_deg > 0.0f) || r->fov_deg >= 360.0f)
         return 0;
-    *c = (float)cos((double)r->fov_deg * VO_PI / 360.0);
+    *c = cos((double)r->fov_deg * VO_PI / 360.0);
     double g[3] = {r->gaze[0], r->gaze[1], r->dims == 3 ? r->gaze[2] : 0.0f};
     if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0)
         g[axis_index(r->normal)] = (double)axis_sign(r->normal);
     double len = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
     for (int k = 0; k < 3; ++k)
-        a[k] = (float)(g[k] / len);
+        a[k] = g[k] / len;
     return 1;
 }
 
-/* Is q inside the cone of patch p?  float32, one rounding per operation
- * (the file is compiled without contraction into fused multiply-adds). */
-static int in_fov(const int64_t q[3], const int64_t p[3], float c, const float a[3], int two_sided)
+/* The cone test in float64 (Section III-B, Table II): q lies in the cone of
+ * patch p iff the angle between r = q - p and the axis a is at most half the
+ * field of view, i.e. a.r >= c |r| (|a.r| for a two-sided target).  The
+ * differences are exact (lattice values), so the only roundings are those
+ * of the dot product, the norm and the product, about 1e-15 |r|.  Returns
+ * the decision; *margin gets (a.r - c |r|) / |r| (0 when q = p). */
+static int in_fov(const int64_t q[3], const int64_t p[3], double c, const double a[3], int two_sided,
+                  double *margin)
 {
-    float rk[3];
+    double rk[3];
     for (int k = 0; k < 3; ++k)
-        rk[k] = (float)q[k] / 1024.0f - (float)p[k] / 1024.0f;   /* both exact; one rounding */
-    float d = a[0] * rk[0] + a[1] * rk[1];
-    d = d + a[2] * rk[2];
+        rk[k] = (double)(q[k] - p[k]) / UNITS_PER_M;
+    double d = a[0] * rk[0] + a[1] * rk[1] + a[2] * rk[2];
     if (two_sided)
-        d = fabsf(d);
-    float rr = rk[0] * rk[0] + rk[1] * rk[1];
-    rr = rr + rk[2] * rk[2];
-    return d >= c * sqrtf(rr);
+        d = fabs(d);
+    double len = sqrt(rk[0] * rk[0] + rk[1] * rk[1] + rk[2] * rk[2]);
+    double m = d - c * len;
+    *margin = len > 0.0 ? m / len : 0.0;
+    return m >= 0.0;
 }
 
-double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint32_t *bits)
+int vo_fov_test(const vo_request *r, const int64_t q[3], const int64_t p[3], double *margin)
+{
+    double c = 0.0, a[3] = {0.0, 0.0, 0.0}, m = 0.0;
+    if (!fov_setup(r, &c, a))
+        return -1;
+    int in = in_fov(q, p, c, a, r->two_sided, &m);
+    if (margin)
+        *margin = m;
+    return in;
+}
+
+double vo_visibility_ex(const vo_scene *s, const vo_request *r, int64_t index, uint32_t *bits, double band[3])
 {
     int64_t q[3];
+    if (band)
+        band[0] = band[1] = band[2] = 0.0;
     if (vo_viewpoint(r, index, q) != 0)
         return NAN;
     if (r->mode == VO_VIEWER)
@@ -253,9 +271,10 @@ double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint
     int an = axis_index(r->normal);
     double sn = (double)axis_sign(r->normal);
     double measure = vo_patch_measure(r);
-    float fov_c = 0.0f, fov_a[3] = {0.0f, 0.0f, 0.0f};
+    double fov_c = 0.0, fov_a[3] = {0.0, 0.0, 0.0};
     int cone = fov_setup(r, &fov_c, fov_a);
     double sum = 0.0, comp = 0.0;   /* Neumaier running sum and compensation */
+    double b_pairs = 0.0, b_in = 0.0, b_out = 0.0;
     int any_blocked = 0;
     for (int64_t j = 0; j < P; ++j) {
         const int64_t *p = pc + 3 * j;
@@ -272,8 +291,6 @@ double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint
             bits[j >> 5] |= 1u << (j & 31);
         if (blocked || !(cos_r > 0.0))
             continue;
-        if (cone && !in_fov(q, p, fov_c, fov_a, r->two_sided))
-            continue;   /* outside the target's field of view */
         double rx = (double)(q[0] - p[0]) / UNITS_PER_M;
         double ry = (double)(q[1] - p[1]) / UNITS_PER_M;
         double rz = (double)(q[2] - p[2]) / UNITS_PER_M;
@@ -283,6 +300,21 @@ double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint
             term = measure * cos_r / (d2 * sqrt(d2));   /* A cos(theta) / d^2 */
         else
             term = measure * cos_r / d2;                /* len cos(theta) / d */
+        if (cone) {
+            double margin;
+            int in = in_fov(q, p, fov_c, fov_a, r->two_sided, &margin);
+            if (fabs(margin) <= VO_FOV_BAND) {
+                /* a float32 evaluation of the cone may decide this pair
+                 * either way */
+                b_pairs += 1.0;
+                if (in)
+                    b_in += term;
+                else
+                    b_out += term;
+            }
+            if (!in)
+                continue;   /* outside the target's field of view */
+        }
         double t = sum + term;
         if (fabs(sum) >= fabs(term))
             comp += (sum - t) + term;
@@ -293,7 +325,17 @@ double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint
     free(pc);
     if (r->mode == VO_STRICT && any_blocked)
         return 0.0;   /* not completely visible: obstructed region */
+    if (band) {
+        band[0] = b_pairs;
+        band[1] = b_in;
+        band[2] = b_out;
+    }
     return sum + comp;
+}
+
+double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint32_t *bits)
+{
+    return vo_visibility_ex(s, r, index, bits, NULL);
 }
 
 typedef struct {
@@ -303,6 +345,7 @@ typedef struct {
     int64_t n;
     double *v_out;
     uint32_t *bits_out;
+    double *band_out;
     int64_t words;
     int tid, threads;
 } vo_job;
@@ -312,13 +355,14 @@ static void *vo_worker(void *arg)
     vo_job *job = (vo_job *)arg;
     for (int64_t i = job->tid; i < job->n; i += job->threads) {
         uint32_t *bits = job->bits_out ? job->bits_out + i * job->words : NULL;
-        job->v_out[i] = vo_visibility(job->s, job->r, job->indices[i], bits);
+        double *band = job->band_out ? job->band_out + 3 * i : NULL;
+        job->v_out[i] = vo_visibility_ex(job->s, job->r, job->indices[i], bits, band);
     }
     return NULL;
 }
 
-int vo_run(const vo_scene *s, const vo_request *r, const int64_t *indices, int64_t n,
-           double *v_out, uint32_t *bits_out, int threads)
+int vo_run_ex(const vo_scene *s, const vo_request *r, const int64_t *indices, int64_t n,
+              double *v_out, uint32_t *bits_out, double *band_out, int threads)
 {
     if (vo_check(s, r) != 0)
         return -1;
@@ -334,7 +378,7 @@ int vo_run(const vo_scene *s, const vo_request *r, const int64_t *indices, int64
     pthread_t tids[256];
     vo_job jobs[256];
     for (int t = 0; t < threads; ++t) {
-        jobs[t] = (vo_job){s, r, indices, n, v_out, bits_out, (P + 31) / 32, t, threads};
+        jobs[t] = (vo_job){s, r, indices, n, v_out, bits_out, band_out, (P + 31) / 32, t, threads};
         pthread_create(&tids[t], NULL, vo_worker, &jobs[t]);
     }
     for (int t = 0; t < threads; ++t)
@@ -343,6 +387,12 @@ int vo_run(const vo_scene *s, const vo_request *r, const int64_t *indices, int64
         if (isnan(v_out[i]))
             return -1;
     return 0;
+}
+
+int vo_run(const vo_scene *s, const vo_request *r, const int64_t *indices, int64_t n,
+           double *v_out, uint32_t *bits_out, int threads)
+{
+    return vo_run_ex(s, r, indices, n, v_out, bits_out, NULL, threads);
 }
 
 double vo_max(const double *v, int64_t n)

@@ -81,18 +81,23 @@ enum { VO_PARTIAL = 0, VO_STRICT = 1, VO_VIEWER = 2 };
  *   around the gaze axis a (Section III-B sets up the visible region as the
  *   part of space inside the field of view, 120 degrees by default, Table II;
  *   Section IV-C turns the gaze).  A patch p counts for q only when q lies in
- *   p's cone.  The decision is a float32 computation that the GPU path makes
- *   in the same way, so both take it identically:
- *     c = (float) cos(fov_deg * pi / 360)            (double, then rounded)
- *     a = (float) (g / |g|) per component             (double, then rounded;
- *                                                      g = gaze, or n if 0)
- *     r_k = q_k - p_k in float metres (k = x, y, z)
- *     d = ((a_x r_x + a_y r_y) + a_z r_z), |d| if two-sided
- *     rr = ((r_x r_x + r_y r_y) + r_z r_z)
- *     inside  iff  d >= c * sqrt(rr)
- *   with every operation a single float32 rounding (no fused multiply-add).
+ *   p's cone, that is when the angle between r = q - p and a is at most
+ *   fov/2:  a.r >= cos(fov/2) |r|  (|a.r| for a two-sided target), with
+ *   a = g / |g| (g = gaze, or the target's normal if gaze is 0).  The oracle
+ *   decides this in float64 on the exact differences r.
+ *   A float32 evaluation of the same inequality (one rounding per operation,
+ *   as the GPU path makes it) errs in the margin a.r - c |r| by at most
+ *   about 10.5 u |r| (u = 2^-24): 5 u from the rounded r, axis, products and
+ *   two sums of the dot product, 5.5 u from the rounded squares, sums, square
+ *   root, cosine and product of the right-hand side.  So it can decide a
+ *   pair differently only where |a.r - c |r|| <= VO_FOV_BAND |r|; those
+ *   pairs are reported by vo_visibility_ex.
  * Strict mode with a cone: 0 if any patch is blocked, else the sum over the
  * patches inside the cone. */
+
+/* Relative cone margin within which a float32 evaluation of the cone test
+ * may differ from the exact one (more than twice the 10.5 u bound above). */
+#define VO_FOV_BAND 1e-6
 
 /* 0 on success, -1 on an invalid request. */
 int vo_check(const vo_scene *s, const vo_request *r);
@@ -115,10 +120,28 @@ int vo_segment_hits_box(int dims, const int64_t q[3], const int64_t p[3],
  * patch j is blocked). */
 double vo_visibility(const vo_scene *s, const vo_request *r, int64_t index, uint32_t *bits);
 
+/* The same; if band != NULL it also receives, over the unblocked patches in
+ * front (those with a term) whose cone margin lies within VO_FOV_BAND of the
+ * cone's edge: band[0] their number, band[1] the sum of the terms of those
+ * counted (inside the cone), band[2] the sum of those left out.  A float32
+ * evaluation of the cone therefore gives a value in
+ * [v - band[1], v + band[2]].  All zero without a cone, and in strict mode
+ * when a patch is blocked (the value is 0 whatever the cone decides). */
+double vo_visibility_ex(const vo_scene *s, const vo_request *r, int64_t index, uint32_t *bits, double band[3]);
+
+/* The cone test for one pair (q, p), in units: 1 inside, 0 outside, -1 if
+ * the request has no cone; *margin (optional) gets (a.r - c |r|) / |r|. */
+int vo_fov_test(const vo_request *r, const int64_t q[3], const int64_t p[3], double *margin);
+
 /* Visibility for n viewpoint indices on `threads` POSIX threads.
  * bits_out (optional) holds n * ceil(P/32) words.  Returns 0 or -1. */
 int vo_run(const vo_scene *s, const vo_request *r, const int64_t *indices, int64_t n,
            double *v_out, uint32_t *bits_out, int threads);
+
+/* The same, with band_out (optional) holding n * 3 doubles of
+ * vo_visibility_ex's band output. */
+int vo_run_ex(const vo_scene *s, const vo_request *r, const int64_t *indices, int64_t n,
+              double *v_out, uint32_t *bits_out, double *band_out, int threads);
 
 /* Largest value of v[0..n). */
 double vo_max(const double *v, int64_t n);

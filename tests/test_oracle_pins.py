@@ -639,6 +639,114 @@ def test_fov_with_strict_mode_and_two_sided():
                     assert two[iy * nx + ix] == two[iy2 * nx + ix]
 
 
+def _angle_to_axis(r, a):
+    """Angle between vectors r and a, by atan2 of the cross and dot products
+    (an independent route to the cone test's cosine inequality)."""
+    cx = r[1] * a[2] - r[2] * a[1]
+    cy = r[2] * a[0] - r[0] * a[2]
+    cz = r[0] * a[1] - r[1] * a[0]
+    return math.atan2(math.sqrt(cx * cx + cy * cy + cz * cz), r[0] * a[0] + r[1] * a[1] + r[2] * a[2])
+
+
+def test_fov_decision_is_the_angle_to_the_axis():
+    """The oracle decides the cone in float64: q is in p's cone iff the angle
+    between q - p and the gaze axis is at most half the field of view (for a
+    two-sided target, the angle to the axis or to its opposite), and the
+    margin it reports has the decision's sign."""
+    rng = np.random.default_rng(41)
+    base = req3((0, 0, 20 * U), pu=4, pw=2)
+    checked = 0
+    for _ in range(3000):
+        fov = float(rng.uniform(5.0, 355.0))
+        g = rng.normal(size=3)
+        two = bool(rng.integers(0, 2))
+        r = dict(_fov(base, fov, tuple(float(x) for x in g)), flags=FLAG_TWO_SIDED if two else 0)
+        q = [int(x) for x in rng.integers(-60 * U, 60 * U, size=3)]
+        p = [int(x) for x in rng.integers(-10 * U, 10 * U, size=3)]
+        inside, margin = O.fov_test(r, q, p)
+        gf = np.asarray(np.float32(g), np.float64)
+        a = gf / np.linalg.norm(gf)
+        rv = [(q[k] - p[k]) / U for k in range(3)]
+        ang = _angle_to_axis(rv, a)
+        if two:
+            ang = min(ang, math.pi - ang)
+        half = math.radians(fov) / 2.0
+        if abs(ang - half) < 1e-9:
+            continue
+        assert inside == (ang <= half), (fov, g, q, p)
+        assert (margin >= 0) == inside
+        checked += 1
+    assert checked > 2900
+    assert O.fov_test(base, [0, 0, 0], [1, 1, 1]) == (None, 0.0)
+
+
+def _f32_cone(q, p, fov, g, two_sided):
+    """The float32 evaluation of the cone test that the request header
+    defines (one rounding per operation, world order x, y, z)."""
+    f = np.float32
+    c = f(math.cos(fov * math.pi / 360.0))
+    gd = [float(f(x)) for x in g]
+    if not any(gd):
+        gd = [0.0, 1.0, 0.0]   # the targets here face +y
+    n = math.sqrt(sum(x * x for x in gd))
+    a = [f(x / n) for x in gd]
+    r = [f(f(q[k] / U) - f(p[k] / U)) for k in range(3)]
+    d = f(f(f(a[0] * r[0]) + f(a[1] * r[1])) + f(a[2] * r[2]))
+    if two_sided:
+        d = abs(d)
+    rr = f(f(f(r[0] * r[0]) + f(r[1] * r[1])) + f(r[2] * r[2]))
+    return bool(d >= f(c * f(np.sqrt(rr))))
+
+
+def test_fov_band_holds_every_pair_a_float32_evaluation_may_flip():
+    """A float32 evaluation of the cone can differ from the float64 decision
+    only within VO_FOV_BAND of the edge (the bound derived in the oracle's
+    header); on exact ties at 45 degrees (r = (k, k, 0) against the +y axis
+    with a 90 degree field of view) the band reports the pair, and the value
+    a float32 cone gives lies in the bracket the band states."""
+    rng = np.random.default_rng(43)
+    base = req3((0, 0, 20 * U), pu=4, pw=2)
+    flips = 0
+    for _ in range(4000):
+        fov = float(rng.choice([60.0, 90.0, 120.0, 150.0, 200.0]))
+        g = (0.0, 1.0, 0.0) if rng.random() < 0.5 else tuple(float(x) for x in rng.normal(size=3))
+        r = _fov(base, fov, g)
+        k = int(rng.integers(1, 40 * U))
+        # near-tie pairs: r close to 45 degrees off the +y axis, and random ones
+        if rng.random() < 0.5:
+            rv = [k + int(rng.integers(-2, 3)), k, int(rng.integers(-2, 3))]
+        else:
+            rv = [int(x) for x in rng.integers(-40 * U, 40 * U, size=3)]
+        p = [int(x) for x in rng.integers(-10 * U, 10 * U, size=3)]
+        q = [p[i] + rv[i] for i in range(3)]
+        inside, margin = O.fov_test(r, q, p)
+        if _f32_cone(q, p, fov, g, False) != inside:
+            flips += 1
+            assert abs(margin) <= 1e-6, (fov, g, q, p, margin)
+    assert flips > 10   # the near ties do flip under float32
+    # a 2D target seen from a point from which some patch directions are
+    # exactly 45 degrees off the normal: the band reports them
+    W, N = 16 * U, 32
+    tgt = req2((0, 0), width=W, pu=N)
+    pc = O.patch_centres(tgt)
+    d = 20 * U
+    q = (int(pc[5][0]) + d, d, 0)          # patch 5 at exactly 45 degrees
+    r = _fov(single_viewpoint(tgt, q), 90.0)
+    v, band = O.run(scene(2, []), r, band=True)
+    assert band[0, 0] >= 1
+    # the value with the float32 cone decisions is inside the bracket
+    v32 = 0.0
+    for j in range(N):
+        p = pc[j]
+        rx, ry = (q[0] - p[0]) / U, (q[1] - p[1]) / U
+        if ry > 0 and _f32_cone(q, p, 90.0, (0.0, 0.0, 0.0), False):
+            v32 += (W / U / N) * ry / (rx * rx + ry * ry)
+    assert v[0] - band[0, 1] - 1e-12 <= v32 <= v[0] + band[0, 2] + 1e-12
+    # no cone, or no pair near the edge: an empty band
+    _, b0 = O.run(scene(2, []), single_viewpoint(tgt, q), band=True)
+    assert not b0.any()
+
+
 def test_blocking_is_convex_in_viewpoint_and_in_patch():
     """The one-box shortcuts rest on two convexity facts, checked here with
     the exact predicate: for a fixed patch point p, if a box blocks the

@@ -68,7 +68,7 @@ def _context(scene, req, bits):
 
 def _same(got, ref, levels):
     compare_v(ref[0], got[0], "static vs context")
-    compare_colors(ref[0], got[1], levels, 0.0)
+    compare_colors(ref[0], got[0], got[1], levels, got[3]["v_ref"], ref[3]["v_ref"])
     if ref[2] is not None:
         compare_bits(ref[2], got[2], "static vs context")
 
