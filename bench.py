@@ -693,10 +693,12 @@ def sub_serve(ctx, args, sampler):
         # FIFO server, one request per launch
         q = _queue.Queue()
         done = [0.0] * n
+        began = [0.0] * n
 
         def worker():
             for _ in range(n):
                 i, t0 = q.get()
+                began[i] = time.perf_counter() - t0
                 fifo_one(picks[i])
                 done[i] = time.perf_counter() - t0
 
@@ -711,8 +713,14 @@ def sub_serve(ctx, args, sampler):
             q.put((i, t0))
         th.join()
         lat = [1e3 * (done[i] - arr[i]) for i in range(n)]
+        slow = np.argsort(lat)[-3:][::-1]
         fifo = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "segments_per_s": seg / max(done), "clocks": sampler.window(t_w, time.monotonic(), "FIFO arm")}
+                "segments_per_s": seg / max(done), "clocks": sampler.window(t_w, time.monotonic(), "FIFO arm"),
+                "median_wait_ms": float(np.median([1e3 * (began[i] - arr[i]) for i in range(n)])),
+                "median_service_ms": float(np.median([1e3 * (done[i] - began[i]) for i in range(n)])),
+                "slowest": [{"latency_ms": lat[i], "wait_ms": 1e3 * (began[i] - arr[i]),
+                             "service_ms": 1e3 * (done[i] - began[i]), "segments": seg_of[i % len(pool)]}
+                            for i in slow]}
 
         # continuous batching through the scheduler
         tickets = [None] * n
@@ -724,15 +732,24 @@ def sub_serve(ctx, args, sampler):
                 time.sleep(arr[i] - now)
             ts = time.perf_counter() - t0   # the library times from here to completion
             tickets[i] = (ctx.vcm_submit(picks[i]), ts)
-        lat2, last = [], 0.0
+        lat2, last, info = [], 0.0, []
         for i, (t, ts) in enumerate(tickets):
             ctx.vcm_poll(t, -1)
             _, hc, _, stt = ctx.vcm_result_get(t, copy=False)
             lat2.append((ts - arr[i]) * 1e3 + stt["latency_ms"])
             last = max(last, arr[i] + lat2[-1] / 1e3)
+            info.append({k: stt[k] for k in ("queue_ms", "device_ms", "group_size", "launch_form")})
             ctx.vcm_result_release(t)
+        slow = np.argsort(lat2)[-3:][::-1]
         cont = {"p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
-                "segments_per_s": seg / last, "clocks": sampler.window(t_w, time.monotonic(), "continuous arm")}
+                "segments_per_s": seg / last, "clocks": sampler.window(t_w, time.monotonic(), "continuous arm"),
+                "persistent_launch_share": float(np.mean([x["launch_form"] == 0 for x in info])),
+                "mean_group_size": float(np.mean([x["group_size"] for x in info])),
+                "median_queue_ms": float(np.median([x["queue_ms"] for x in info])),
+                "median_device_ms": float(np.median([x["device_ms"] for x in info])),
+                "median_host_ms": float(np.median([lat2[i] - info[i]["queue_ms"] - info[i]["device_ms"]
+                                                   for i in range(n)])),
+                "slowest": [dict(latency_ms=lat2[i], segments=seg_of[i % len(pool)], **info[i]) for i in slow]}
         out.append({"rate_per_s": rate, "requests": n, "continuous": cont, "one_per_launch_fifo": fifo})
     ctx.vcm_set_slots(4, 64)
     return {"workload": "Poisson arrivals of requests from the batched mix against a resident 100,000-box scene",
@@ -945,21 +962,35 @@ def run_modes(args):
 EQUIVISIBLE_WORKLOAD = "2D, 10 m target, 1024 x 1024 cells over 1 km, no obstacles, 16 levels"
 
 
-def equivisible_dense(ctx, S=10.0, n=1024, half=500.0, levels=16, samples=64):
-    """The dense GPU map of a 2D segment target of length S at the origin
-    facing +y over an n x n grid of 2 half metres a side, no obstacles.
-    Returns (request, device v, colours, cell-centre x, y as numpy)."""
+def equivisible_request(S=10.0, n=1024, half=500.0, levels=16, samples=64):
+    """An empty 2D scene and the request of a segment target of length S at
+    the origin facing +y over an n x n grid of 2 half metres a side."""
     import synth
 
     scene = synth.Scene(2, np.zeros((0, 3), np.int64), np.zeros((0, 3), np.int64))
     req = synth.make_request(2, (0.0, 0.0), synth.AXIS_PX, synth.AXIS_PY, S, samples, (-half, -half),
                              (2 * half / n, 2 * half / n), (n, n), color_levels=levels)
+    return scene, req
+
+
+def grid_centres(req):
+    """Cell-centre x and y (metres) of a request's grid, flattened in output order."""
+    n = req["grid_nx"]
+    xs = (req["grid_origin"][0] + (np.arange(n) + 0.5) * req["grid_step"][0]) / 1024.0
+    ys = (req["grid_origin"][1] + (np.arange(req["grid_ny"]) + 0.5) * req["grid_step"][1]) / 1024.0
+    X, Y = np.meshgrid(xs, ys)
+    return X.ravel(), Y.ravel()
+
+
+def equivisible_dense(ctx, S=10.0, n=1024, half=500.0, levels=16, samples=64):
+    """The dense GPU map of equivisible_request's target, no obstacles.
+    Returns (request, device v, colours, cell-centre x, y as numpy)."""
+    scene, req = equivisible_request(S, n, half, levels, samples)
     ctx.load_scene(scene)
     ctx.vcm_build(0.0)
     v, c, _, _ = ctx.compute(req)
-    xs = -half + (np.arange(n) + 0.5) * (2 * half / n)
-    X, Y = np.meshgrid(xs, xs)
-    return req, v, c.cpu().numpy().astype(np.int64), X.ravel(), Y.ravel()
+    X, Y = grid_centres(req)
+    return req, v, c.cpu().numpy().astype(np.int64), X, Y
 
 
 def equivisible_row(c_dense, X, Y, mu, S=10.0, levels=16, d0=1.0):

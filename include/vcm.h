@@ -126,26 +126,46 @@ typedef struct {
      * Table II; Section IV-C turns the gaze).  fov_deg in (0, 360): patch p
      * counts for viewpoint q only if q lies in p's cone of half-angle
      * fov_deg / 2 around the axis `gaze` (world x, y, z; all 0 = the
-     * target's facing normal; z ignored in 2D).  0 or >= 360: no cone.  The
-     * test is a float32 computation with one rounding per operation, in
-     * this order, with r = q - p per world axis in metres:
+     * target's facing normal; z ignored in 2D), i.e. with r = q - p and
+     * a = g / |g|:  a.r >= cos(fov_deg / 2) |r|  (|a.r| with VCM_TWO_SIDED).
+     * 0 or >= 360: no cone.  The kernels evaluate the inequality in float32
+     * with one rounding per operation, in this order (world x, y, z):
      *   c = (float) cos(fov_deg * pi / 360)        (in double, then rounded)
      *   a = (float) (g / |g|) per component         (in double, then rounded)
      *   d = (a.x r.x + a.y r.y) + a.z r.z, |d| with VCM_TWO_SIDED
      *   inside iff d >= c * sqrt((r.x r.x + r.y r.y) + r.z r.z)
-     * In strict mode a viewpoint still gets 0 if any patch is blocked, and
-     * otherwise the sum over the patches inside the cone.  Not with
-     * VCM_VIEWER. */
+     * which errs in the margin a.r - c |r| by at most about 10.5 u |r|
+     * (u = 2^-24), so it can differ from the exact decision only for pairs
+     * within 1e-6 |r| of the cone's edge.  In strict mode a viewpoint still
+     * gets 0 if any patch is blocked, and otherwise the sum over the patches
+     * inside the cone.  Not with VCM_VIEWER. */
     float fov_deg;
     float gaze[3];
 } vcm_request;
+
+/* Values of vcm_stats.error: a device-side failure; a request whose error
+ * is nonzero has an incomplete result.
+ * VCM_DEVERR_BOUNDS:     a bounds check of a checked build (libvcm_checked,
+ *                        compiled with VCM_CHECKED) failed; the access was
+ *                        skipped instead of made.
+ * VCM_DEVERR_SPILL_WAIT: a block of a launch that shares the GPU with other
+ *                        launches gave up its bounded wait for a spill region
+ *                        (a buffer for candidate lists longer than shared
+ *                        memory holds) and cut such a list short.  vcm_poll
+ *                        reports it as VCM_E_TIMEOUT.
+ * The direct calls (vcm_compute, vcm_compute_batch, vcm_compute_static,
+ * vcm_recolor) return once their work is enqueued: the caller finds a
+ * failure in the error word of d_stats after the stream has run.  Their
+ * launches own their spill regions, so only VCM_DEVERR_BOUNDS can occur
+ * there. */
+enum { VCM_DEVERR_NONE = 0, VCM_DEVERR_BOUNDS = 1, VCM_DEVERR_SPILL_WAIT = 2 };
 
 /* Per-request counters written by the device. */
 typedef struct {
     float v_ref;                       /* the v_ref used for colors */
     uint32_t vmax_bits;                /* largest v (float bits), accumulated on device */
     uint32_t edge_cells;               /* viewpoints within 1e-5 (relative) of a color bin edge */
-    uint32_t error;                    /* nonzero: a device-side check failed (see vcm_last_error) */
+    uint32_t error;                    /* VCM_DEVERR_*: nonzero if a device-side check failed */
     unsigned long long slab_tests;     /* lane-level slab tests executed in the row sweep */
     unsigned long long rechecked;      /* segment-box pairs re-decided by the exact float64 predicate */
     unsigned long long segments;       /* viewpoint-patch pairs decided (= viewpoints x patches) */
@@ -167,7 +187,19 @@ typedef struct {
     uint32_t words_per_viewpoint;
     vcm_stats stats;
     double latency_ms;         /* submit -> completion observed by the context */
+    double queue_ms;           /* submit -> its launch began (admission and queueing) */
+    double device_ms;          /* device time of the launch that ran it (its whole group, with the
+                                  copies of results to host memory) */
+    uint32_t group_size;       /* requests in that launch */
+    uint32_t launch_form;      /* VCM_FORM_* of that launch */
 } vcm_result;
+
+/* How the scheduler launched a group (vcm_result.launch_form).
+ * VCM_FORM_PERSISTENT: a persistent grid with the chunk pass, taken when no
+ *   other request waits for a slot.
+ * VCM_FORM_ONE_TILE:   one block per tile, taken while requests wait, so
+ *   that launches on other slots interleave with it block by block. */
+enum { VCM_FORM_PERSISTENT = 0, VCM_FORM_ONE_TILE = 1 };
 
 /* Autotuned launch shape for one class of request (see vcm_autotune). */
 typedef struct {
@@ -179,12 +211,16 @@ typedef struct {
 /* ---- context --------------------------------------------------------- */
 
 /* Create a context on CUDA device `device`.  mem_budget_bytes bounds the
- * device memory that admitted requests may hold at once (0 = 64 GiB).
- * The context owns the device scene, its index, streams and scratch: per
- * execution slot (and one for direct calls) a descriptor buffer, a spill
- * list of n_boxes ints per resident block, and a 13 MB work buffer through
- * which the blocks of a launch share the open viewpoints of expensive tiles;
- * none of these count against the budget. */
+ * device memory of the asynchronous path (0 = 64 GiB): the result buffers
+ * of admitted requests, the occlusion bits kept for recolouring
+ * (VCM_CACHE_BITS), and the scratch of the scheduler's execution slots.
+ * A slot's scratch is a descriptor buffer, a spill list of n_boxes ints per
+ * block that can be resident (about 304 MB per slot for 100,000 boxes on
+ * 152 SMs) and a 13 MB work buffer through which the blocks of a launch
+ * share the open viewpoints of expensive tiles; it is allocated when the
+ * slot first runs a launch that needs it and kept.  The direct path
+ * (vcm_compute, vcm_compute_batch, vcm_recolor) has scratch of its own,
+ * which the budget does not count. */
 vcm_status vcm_ctx_create(int device, size_t mem_budget_bytes, vcm_ctx **out);
 
 /* Wait for all work of the context, then free everything it owns. */
@@ -233,15 +269,22 @@ vcm_status vcm_compute(vcm_ctx *ctx, const vcm_request *req, float *d_v, uint8_t
 
 /* Queue a request.  Non-blocking: a scheduler thread admits queued requests
  * as execution slots and budgeted memory free up, and runs each admitted
- * group as one persistent batched launch while other groups are still on
- * the device.  VCM_E_NOMEM if the request alone exceeds the budget. */
+ * group as one batched launch while other groups are still on the device.
+ * A launch whose parameters equal those of the slot's previous launch of
+ * the same form is replayed from a CUDA graph captured then; others are
+ * launched directly.  VCM_E_NOMEM if the request's results together with
+ * one slot's scratch exceed the budget. */
 vcm_status vcm_submit(vcm_ctx *ctx, const vcm_request *req, uint64_t *ticket);
 
 /* Queue several requests that must run together in one batched launch. */
 vcm_status vcm_submit_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, uint64_t *tickets);
 
 /* VCM_OK when finished, VCM_PENDING if still queued or running after
- * waiting up to wait_ms (-1 = forever), or the request's error. */
+ * waiting up to wait_ms (-1 = forever), or the request's error: VCM_E_NOMEM
+ * (its buffers could not be allocated with nothing else in flight),
+ * VCM_E_CUDA (a launch or copy failed, or a device-side bounds check),
+ * VCM_E_TIMEOUT (a bounded device-side wait gave up, VCM_DEVERR_SPILL_WAIT),
+ * VCM_E_CANCELLED. */
 vcm_status vcm_poll(vcm_ctx *ctx, uint64_t ticket, int32_t wait_ms);
 
 /* Results of a finished request (host copies and device buffers). */
@@ -256,6 +299,29 @@ vcm_status vcm_cancel(vcm_ctx *ctx, uint64_t ticket);
 /* Scheduler limits: number of execution slots (streams; 1..16) and the
  * largest number of requests merged into one launch. */
 vcm_status vcm_set_slots(vcm_ctx *ctx, uint32_t slots, uint32_t max_batch);
+
+/* Device memory of the asynchronous path, in bytes. */
+typedef struct {
+    uint64_t budget;             /* the context's budget */
+    uint64_t results;            /* result buffers of admitted requests not yet released */
+    uint64_t slot_scratch;       /* scratch the scheduler's slots hold now */
+    uint64_t slot_scratch_need;  /* scratch one slot needs for the current scene (counted
+                                    against the budget before a slot first runs) */
+} vcm_memory;
+vcm_status vcm_get_memory(vcm_ctx *ctx, vcm_memory *out);
+
+/* Host-side fault injection, for testing how failures surface (nothing
+ * here faults or stalls the GPU).
+ * VCM_INJECT_SPILL_BUSY: the next `count` launches of the scheduler run one
+ *   block per tile with every spill region already marked held and a claim
+ *   limit of 8 rounds (microseconds), so a tile whose candidate list is
+ *   longer than shared memory holds gives up its bounded wait: its request
+ *   finishes with VCM_E_TIMEOUT.
+ * VCM_INJECT_ALLOC_FAIL: the next `count` device allocations of request
+ *   buffers by the scheduler fail as if the device had no memory left.
+ * VCM_INJECT_NONE with count 0 clears both. */
+enum { VCM_INJECT_NONE = 0, VCM_INJECT_SPILL_BUSY = 1, VCM_INJECT_ALLOC_FAIL = 2 };
+vcm_status vcm_inject(vcm_ctx *ctx, uint32_t kind, uint32_t count);
 
 /* ---- batching and tuning --------------------------------------------- */
 

@@ -8,6 +8,8 @@
 // memory-budget admission (continuous batching).
 #include "vcm_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -31,6 +33,15 @@ struct Ticket;   // one asynchronous request (defined below)
 namespace {
 
 thread_local std::string t_err;
+
+// An NVTX range over a host stage (visible to nsys / ncu --nvtx; a no-op
+// when no tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 vcm_status fail(vcm_status s, const char *fmt, ...)
 {
@@ -153,6 +164,7 @@ vcm_status canonicalise_viewer(const vcm_request *r, Canon &c)
 
 vcm_status canonicalise(const vcm_request *r, Canon &c)
 {
+    Range range("vcm canonicalise");
     if (!r)
         return fail(VCM_E_ARG, "request is NULL");
     if (r->dims != 2 && r->dims != 3)
@@ -431,9 +443,13 @@ struct Slot {
     // completion: the slot's waiter thread blocks on `done` (without any
     // lock held), then marks the in-flight group finished
     cudaEvent_t done = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;   // device time of the in-flight launch
     std::vector<std::shared_ptr<::Ticket>> inflight;
     bool posted = false;
     std::thread waiter;
+    bool scheduler = false;   // one of the scheduler's slots (its scratch counts against the budget)
+    double work = 0.0;        // segments of the in-flight group
+    size_t scratch = 0;       // bytes of scratch the slot holds
     // graphs of the device work of one batched launch, one per launch form
     // (0: one block per tile, 1: persistent with the chunk pass)
     cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -441,6 +457,10 @@ struct Slot {
     // everything a form's graph was captured with (parameters, buffers,
     // scene); an equal key replays the graph as it is
     std::vector<unsigned long long> key[2];
+    // the parameters of the slot's previous launch of each form: a launch
+    // equal to it is captured (it is likely to come again), others run
+    // directly
+    std::vector<unsigned long long> last_key[2];
 };
 
 struct Layout {
@@ -495,6 +515,10 @@ struct vcm_ctx {
     std::thread worker;
     bool stop = false;
     int running_groups = 0;
+    size_t scratch = 0;   // scratch held by the scheduler's slots (counted against the budget)
+    // host-side fault injection (vcm_inject): launches with every spill
+    // region held, and failing request-buffer allocations, still to come
+    uint32_t inject_spill = 0, inject_alloc = 0;
 };
 
 namespace {
@@ -519,7 +543,9 @@ struct Ticket {
     vcm_stats *h_stats = nullptr;
     size_t bytes = 0;
     Slot *slot = nullptr;
-    std::chrono::steady_clock::time_point t_submit, t_done;
+    std::chrono::steady_clock::time_point t_submit, t_launch, t_done;
+    double device_ms = 0.0;
+    uint32_t group_size = 0, form = 0;
 };
 
 namespace {
@@ -636,9 +662,36 @@ void fill_desc(char *h, const char *d_base, const Layout &L, const std::vector<c
     vps[n] = vp;
 }
 
-vcm_status ensure_slot(vcm_ctx *ctx, Slot &s, size_t desc_bytes, size_t n_stats, int grid_blocks,
-                       cudaStream_t sync_stream)
+// Device bytes of a slot's scratch.
+size_t slot_bytes(const Slot &s)
 {
+    return s.desc_cap + (s.d_work ? kWorkBytes : 0) + (s.spill_cap + s.spill_busy_cap) * sizeof(int) +
+           s.stats_cap * sizeof(vcm_stats);
+}
+
+// Scratch one scheduler slot needs for the current scene: the work arena,
+// a spill list of n_boxes ints for every block that can be resident (at the
+// smallest shared-memory size, the most blocks), their claim words, 256
+// stats entries and 1 MB of descriptors.
+size_t slot_scratch_need(const vcm_ctx *ctx)
+{
+    const size_t blocks = (size_t)tiles_blocks_per_sm(32) * (size_t)ctx->sm_count;
+    return kWorkBytes + blocks * (std::max<uint32_t>(ctx->n_boxes, 1) + 1) * sizeof(int) + 256 * sizeof(vcm_stats) +
+           ((size_t)1 << 20);
+}
+
+vcm_status ensure_slot_impl(vcm_ctx *ctx, Slot &s, size_t desc_bytes, size_t n_stats, int grid_blocks,
+                            cudaStream_t sync_stream)
+{
+    if (s.scheduler) {
+        // A scheduler slot takes its whole scratch for the scene at its
+        // first launch (what admission charged: slot_scratch_need), so a
+        // later, larger launch does not regrow it: a cudaFree would wait
+        // for the device while the context lock is held.
+        grid_blocks = std::max(grid_blocks, tiles_blocks_per_sm(32) * ctx->sm_count);
+        desc_bytes = std::max<size_t>(desc_bytes, (size_t)1 << 19);
+        n_stats = std::max<size_t>(n_stats, 256);
+    }
     const size_t spill_need = (size_t)grid_blocks * std::max<uint32_t>(ctx->n_boxes, 1);
     const bool grow = desc_bytes > s.desc_cap || spill_need > s.spill_cap || n_stats > s.stats_cap ||
                       !s.d_work || (size_t)grid_blocks > s.spill_busy_cap;
@@ -696,9 +749,24 @@ vcm_status ensure_slot(vcm_ctx *ctx, Slot &s, size_t desc_bytes, size_t n_stats,
     return VCM_OK;
 }
 
+// Grow a slot's scratch as a launch needs it; a scheduler slot's bytes are
+// kept in the context's count, which admission charges against the budget.
+vcm_status ensure_slot(vcm_ctx *ctx, Slot &s, size_t desc_bytes, size_t n_stats, int grid_blocks,
+                       cudaStream_t sync_stream)
+{
+    const vcm_status st = ensure_slot_impl(ctx, s, desc_bytes, n_stats, grid_blocks, sync_stream);
+    const size_t now = slot_bytes(s);
+    if (s.scheduler)
+        ctx->scratch = ctx->scratch - s.scratch + now;
+    s.scratch = now;
+    return st;
+}
+
+// Staged boxes of a launch: the largest of its requests' shapes (at least
+// 32, the smallest vcm_set_tune takes).
 int launch_box_cap(const std::vector<vcm_tune> &shapes)
 {
-    uint32_t cap = 256;
+    uint32_t cap = 32;
     for (auto &t : shapes)
         cap = std::max(cap, t.box_cap);
     return (int)std::min<uint32_t>(cap, 5000);
@@ -728,6 +796,7 @@ vcm_status prepare_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *
                           const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
                           uint32_t *const *bits, vcm_stats *stats, cudaStream_t sync_stream, Prepared &P)
 {
+    Range range("vcm prepare launch");
     if (!ctx->built)
         return fail(VCM_E_STATE, "vcm_build has not been called for the current scene");
     P.L = layout_for(cs, shapes);
@@ -754,8 +823,10 @@ vcm_status prepare_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *
 // kernel and the quantiser, in stream order.  The node sequence is the same
 // for every launch, so a captured graph can be updated in place.
 vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *stats, cudaStream_t stream,
-                         bool timed = false, bool capturing = false, bool one_tile = false)
+                         bool timed = false, bool capturing = false, bool one_tile = false,
+                         int claim_rounds = kClaimRounds, bool hold_spill = false)
 {
+    Range range("vcm record launch");
     CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, P.L.bytes, cudaMemcpyHostToDevice, stream));
     // An event recorded inside a stream capture cannot be waited on later;
     // a captured launch records it after the graph launch instead.
@@ -767,13 +838,18 @@ vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *st
     const long long *d_vps = reinterpret_cast<const long long *>(s.d_desc + P.L.off_vps);
     (void)stats;   // the descriptors point into it; the prologue clears it
     CUDA_TRY(launch_prologue(d_reqs, (int)P.n, s.d_work, P.any_bits, stream));
+    // fault injection: every spill region already held (any nonzero word)
+    if (hold_spill)
+        CUDA_TRY(cudaMemsetAsync(s.d_spill_busy, 1, s.spill_busy_cap * sizeof(int), stream));
     if (timed && ctx->ev_before)
         CUDA_TRY(cudaEventRecord(ctx->ev_before, stream));
     CUDA_TRY(launch_tiles(ctx->scene, d_reqs, d_tiles, (int)P.n, P.L.total_tiles, s.d_work, s.d_spill,
                           P.blocks, P.box_cap, P.extra, P.tile_check, stream, one_tile, s.d_spill_busy,
-                          /*share=*/true));
+                          /*share=*/true, claim_rounds));
     if (timed && ctx->ev_after)
         CUDA_TRY(cudaEventRecord(ctx->ev_after, stream));
+    if (hold_spill)
+        CUDA_TRY(cudaMemsetAsync(s.d_spill_busy, 0, s.spill_busy_cap * sizeof(int), stream));
     CUDA_TRY(launch_quantise(d_reqs, d_vps, (int)P.n, P.L.total_vp, stream));
     return VCM_OK;
 }
@@ -789,11 +865,16 @@ vcm_status enqueue_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *
     return record_launch(ctx, s, P, stats, stream, timed);
 }
 
-// Same device work, captured into the slot's graph (updated in place when
-// the topology allows, re-instantiated otherwise) and launched.
+// Same device work on the slot's stream.  A launch whose parameters equal
+// those the form's graph was captured with replays the graph; one equal to
+// the previous launch of the form (so likely to come again) is captured
+// into the graph (updated in place when the topology allows, re-instantiated
+// otherwise) and launched; any other runs directly, which costs less than a
+// capture that would not be replayed.  `direct_only` launches directly.
 vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *> &cs,
                          const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
-                         uint32_t *const *bits, vcm_stats *stats, bool one_tile)
+                         uint32_t *const *bits, vcm_stats *stats, bool one_tile, bool direct_only = false,
+                         int claim_rounds = kClaimRounds, bool hold_spill = false)
 {
     Prepared P;
     vcm_status st = prepare_launch(ctx, s, cs, shapes, v, color, bits, stats, s.stream, P);
@@ -811,10 +892,15 @@ vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *>
         (unsigned long long)P.blocks, P.n, (unsigned long long)P.extra, (unsigned long long)P.any_bits,
         (unsigned long long)P.tile_check, ptr(s.d_desc), ptr(s.h_desc), ptr(s.d_work), ptr(s.d_spill),
         ptr(s.d_spill_busy), ptr(stats)};
-    if (s.exec[f] && s.key[f] == key) {
+    if (!direct_only && s.exec[f] && s.key[f] == key) {
         CUDA_TRY(cudaGraphLaunch(s.exec[f], s.stream));
         CUDA_TRY(cudaEventRecord(s.desc_copied, s.stream));
         return VCM_OK;
+    }
+    if (direct_only || s.last_key[f] != key) {
+        if (!direct_only)
+            s.last_key[f] = key;
+        return record_launch(ctx, s, P, stats, s.stream, false, false, one_tile, claim_rounds, hold_spill);
     }
     s.key[f].clear();
     CUDA_TRY(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeRelaxed));
@@ -909,17 +995,28 @@ void slot_waiter(vcm_ctx *ctx, Slot *s)
         cudaEvent_t ev = s->done;
         lk.unlock();
         const cudaError_t e = cudaEventSynchronize(ev);
-        lk.lock();
         const auto now = std::chrono::steady_clock::now();
+        float dev_ms = 0.f;
+        if (e == cudaSuccess && cudaEventElapsedTime(&dev_ms, s->t0, s->t1) != cudaSuccess) {
+            cudaGetLastError();
+            dev_ms = 0.f;
+        }
+        lk.lock();
         for (auto &t : group) {
+            t->device_ms = dev_ms;
+            const uint32_t derr = t->h_stats ? t->h_stats->error : 0u;
             if (e != cudaSuccess) {
                 t->state = T_ERROR;
                 t->err = VCM_E_CUDA;
                 t->msg = std::string("launch failed: ") + cudaGetErrorString(e);
-            } else if (t->h_stats && t->h_stats->error) {
+            } else if (derr == VCM_DEVERR_SPILL_WAIT) {
+                t->state = T_ERROR;
+                t->err = VCM_E_TIMEOUT;
+                t->msg = "a bounded device-side wait for a spill region gave up; the result is incomplete";
+            } else if (derr) {
                 t->state = T_ERROR;
                 t->err = VCM_E_CUDA;
-                t->msg = "device-side check failed";
+                t->msg = "device-side bounds check failed (error " + std::to_string(derr) + ")";
             } else {
                 t->state = T_DONE;
             }
@@ -953,6 +1050,10 @@ void release_buffers(vcm_ctx *ctx, Ticket &t)
 // Layout: v (floats) | color | bits | stats.
 bool alloc_buffers(vcm_ctx *ctx, Ticket &t, cudaStream_t stream)
 {
+    if (ctx->inject_alloc > 0) {   // vcm_inject: this allocation fails
+        --ctx->inject_alloc;
+        return false;
+    }
     const Canon &c = t.canon;
     const size_t n = (size_t)c.n_vp;
     const size_t off_color = align_up(n * 4, 256);
@@ -983,6 +1084,7 @@ bool alloc_buffers(vcm_ctx *ctx, Ticket &t, cudaStream_t stream)
 // Launch one admitted group on its slot (called with ctx->mu held).
 void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &group)
 {
+    Range range("vcm launch group");
     std::vector<const Canon *> cs;
     std::vector<vcm_tune> shapes;
     std::vector<float *> v;
@@ -996,13 +1098,26 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
         bits.push_back(t->d_bits);
     }
     vcm_status st = ensure_slot(ctx, s, 0, group.size(), 1, s.stream);
-    // One block per tile while other work runs or waits, so that launches of
-    // other slots interleave with it block by block; a group that starts with
-    // nothing else in flight or queued gets the persistent grid and its chunk
-    // pass (a request that arrives meanwhile waits for it).
-    const bool alone = ctx->running_groups == 0 && ctx->queue.empty();
+    // The persistent grid and its chunk pass on an idle GPU: a request
+    // that arrives meanwhile runs as soon as SMs free up, as it would
+    // behind a FIFO.  One block per tile while other launches run, so that
+    // they interleave block by block instead of one waiting for the other
+    // to drain.
+    const bool inject = ctx->inject_spill > 0;
+    if (inject)
+        --ctx->inject_spill;
+    const bool one_tile = inject || ctx->running_groups > 0;
+    const auto now = std::chrono::steady_clock::now();
+    for (auto &t : group) {
+        t->t_launch = now;
+        t->group_size = (uint32_t)group.size();
+        t->form = one_tile ? VCM_FORM_ONE_TILE : VCM_FORM_PERSISTENT;
+    }
+    if (st == VCM_OK && cudaEventRecord(s.t0, s.stream) != cudaSuccess)
+        st = fail(VCM_E_CUDA, "cudaEventRecord failed");
     if (st == VCM_OK)
-        st = enqueue_graph(ctx, s, cs, shapes, v.data(), col.data(), bits.data(), s.d_stats, !alone);
+        st = enqueue_graph(ctx, s, cs, shapes, v.data(), col.data(), bits.data(), s.d_stats, one_tile,
+                           /*direct_only=*/inject, inject ? 8 : kClaimRounds, /*hold_spill=*/inject);
     if (st == VCM_OK) {
         for (size_t i = 0; i < group.size(); ++i) {
             Ticket &t = *group[i];
@@ -1014,12 +1129,15 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
                                 s.stream);
             cudaMemcpyAsync(t.h_stats, s.d_stats + i, sizeof(vcm_stats), cudaMemcpyDeviceToHost, s.stream);
         }
-        if (cudaEventRecord(s.done, s.stream) == cudaSuccess) {
+        if (cudaEventRecord(s.t1, s.stream) == cudaSuccess && cudaEventRecord(s.done, s.stream) == cudaSuccess) {
             for (auto &t : group) {
                 t->state = T_RUNNING;
                 t->slot = &s;
             }
             s.inflight = group;
+            s.work = 0.0;
+            for (auto &t : group)
+                s.work += (double)t->canon.n_vp * t->canon.P;
             s.posted = true;
             s.busy = true;
             ctx->running_groups++;
@@ -1038,34 +1156,104 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
 
 enum SchedStep { STEP_WAIT, STEP_LAUNCHED, STEP_PROGRESS };
 
+// Free the scratch of an idle scheduler slot (and the graphs that use it);
+// the next launch on the slot allocates it again.  Only with nothing in
+// flight on the slot.
+void release_slot_scratch(vcm_ctx *ctx, Slot &s)
+{
+    for (int f = 0; f < 2; ++f) {
+        if (s.exec[f]) cudaGraphExecDestroy(s.exec[f]);
+        if (s.graph[f]) cudaGraphDestroy(s.graph[f]);
+        s.exec[f] = nullptr;
+        s.graph[f] = nullptr;
+        s.key[f].clear();
+        s.last_key[f].clear();
+    }
+    cudaStreamSynchronize(s.stream);
+    if (s.d_desc) cudaFree(s.d_desc);
+    if (s.h_desc) cudaFreeHost(s.h_desc);
+    if (s.d_work) cudaFree(s.d_work);
+    if (s.d_spill) cudaFree(s.d_spill);
+    if (s.d_spill_busy) cudaFree(s.d_spill_busy);
+    if (s.d_stats) cudaFree(s.d_stats);
+    s.d_desc = s.h_desc = nullptr;
+    s.d_work = s.d_spill = s.d_spill_busy = nullptr;
+    s.d_stats = nullptr;
+    s.desc_cap = s.spill_cap = s.spill_busy_cap = s.stats_cap = 0;
+    if (s.scheduler)
+        ctx->scratch -= s.scratch;
+    s.scratch = 0;
+}
+
 // One scheduling decision (ctx->mu held): admit a batch from the head of the
 // queue onto a free slot and launch it.  Called by the scheduler thread and,
 // once, inline by vcm_submit so that a request that can start at once does
 // not wait for a thread hand-off.
+//
+// Admission charges the budget with the result buffers of admitted requests
+// and the scratch of the slots, including what the chosen slot still has to
+// allocate for its first launch.
 SchedStep schedule_once(vcm_ctx *ctx)
 {
+    if (ctx->queue.empty())
+        return STEP_WAIT;
     // Small work goes to a free high-priority slot (its blocks start as
     // soon as blocks of a running big launch finish); big work to a
     // low-priority one.  Either may use the other kind when that is all
     // that is free.
     double head_work = 0.0;
-    if (!ctx->queue.empty())
-        for (auto &t : ctx->queue.front())
-            head_work += (double)t->canon.n_vp * t->canon.P;
+    size_t head_need = 0;
+    for (auto &t : ctx->queue.front()) {
+        head_work += (double)t->canon.n_vp * t->canon.P;
+        head_need += t->canon.out_bytes() + 1024;
+    }
     const bool small = head_work <= kSmallWork;
-    Slot *free_slot = nullptr;
-    for (int pass = 0; pass < 2 && !free_slot; ++pass)
+    // A big head waits while only small groups run: they end soon, and it
+    // then gets the persistent grid on an idle GPU, which runs it faster
+    // than one block per tile beside them.
+    if (!small && ctx->running_groups > 0) {
+        double running_max = 0.0;
         for (auto &s : ctx->slots)
-            if (!s->busy && (pass == 1 || s->high_priority == small)) {
-                free_slot = s.get();
-                break;
-            }
-    if (ctx->queue.empty() || !free_slot)
-        return STEP_WAIT;
+            if (s->busy)
+                running_max = std::max(running_max, s->work);
+        if (running_max <= kSmallWork)
+            return STEP_WAIT;
+    }
+    const size_t scratch_need = slot_scratch_need(ctx);
+    auto growth = [&](const Slot *s) { return scratch_need > s->scratch ? scratch_need - s->scratch : 0; };
+    Slot *free_slot = nullptr;
+    bool any_free = false;
+    for (int trimmed = 0; trimmed < 2 && !free_slot; ++trimmed) {
+        // free slots by preference (matching priority, then any); the first
+        // whose scratch growth and the head's results fit the budget
+        for (int pass = 0; pass < 2 && !free_slot; ++pass)
+            for (auto &s : ctx->slots)
+                if (!s->busy && (pass == 1 || s->high_priority == small)) {
+                    any_free = true;
+                    if (ctx->used + ctx->scratch + growth(s.get()) + head_need <= ctx->budget) {
+                        free_slot = s.get();
+                        break;
+                    }
+                }
+        if (free_slot || !any_free || trimmed || ctx->running_groups > 0)
+            break;
+        // Nothing runs and the head does not fit: give back the scratch of
+        // idle slots, keeping one slot's, and try again.
+        Slot *keep = nullptr;
+        for (auto &s : ctx->slots)
+            if (!keep || s->scratch > keep->scratch)
+                keep = s.get();
+        for (auto &s : ctx->slots)
+            if (s.get() != keep && s->scratch)
+                release_slot_scratch(ctx, *s);
+    }
+    if (!free_slot)
+        return STEP_WAIT;   // finished results still hold memory until released
     // admit groups from the front of the queue while memory allows
     std::vector<std::shared_ptr<Ticket>> batch;
     bool alloc_failed = false;
     double batch_work = 0.0;
+    const size_t slot_growth = growth(free_slot);
     while (!ctx->queue.empty()) {
         auto &grp = ctx->queue.front();
         size_t need = 0;
@@ -1079,7 +1267,7 @@ SchedStep schedule_once(vcm_ctx *ctx)
         // a batch completes as a whole: keep small requests out of big batches
         if (!batch.empty() && batch_work + work > kBatchWork)
             break;
-        if (ctx->used + need > ctx->budget)
+        if (ctx->used + ctx->scratch + slot_growth + need > ctx->budget)
             break;
         bool ok = true;
         for (auto &t : grp) {
@@ -1102,9 +1290,8 @@ SchedStep schedule_once(vcm_ctx *ctx)
         ctx->queue.pop_front();
     }
     if (batch.empty()) {
-        // The head does not fit the budget: finished results still hold
-        // memory until released, so wait.  Only a device allocation that
-        // fails with nothing in flight is final.
+        // Only a device allocation that fails with nothing in flight is
+        // final; otherwise wait for memory to free up.
         if (alloc_failed && ctx->running_groups == 0) {
             auto grp = ctx->queue.front();
             ctx->queue.pop_front();
@@ -1147,6 +1334,9 @@ vcm_status start_scheduler(vcm_ctx *ctx, uint32_t n_slots)
                                               s->high_priority ? prio_high : prio_low));
         CUDA_TRY(cudaEventCreateWithFlags(&s->desc_copied, cudaEventDisableTiming));
         CUDA_TRY(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreate(&s->t0));
+        CUDA_TRY(cudaEventCreate(&s->t1));
+        s->scheduler = true;
         ctx->slots.push_back(std::move(s));
     }
     ctx->stop = false;
@@ -1187,6 +1377,9 @@ void destroy_slot(Slot &s)
     if (s.d_stats) cudaFree(s.d_stats);
     if (s.desc_copied) cudaEventDestroy(s.desc_copied);
     if (s.done) cudaEventDestroy(s.done);
+    if (s.t0) cudaEventDestroy(s.t0);
+    if (s.t1) cudaEventDestroy(s.t1);
+    s.t0 = s.t1 = nullptr;
     if (s.stream) cudaStreamDestroy(s.stream);
     s.inflight.clear();
     s.stream = nullptr;
@@ -1197,6 +1390,7 @@ void destroy_slot(Slot &s)
     s.spill_cap = s.spill_busy_cap = 0;
     s.d_stats = nullptr;
     s.stats_cap = 0;
+    s.scratch = 0;
     s.busy = s.posted = false;
     s.graph[0] = s.graph[1] = nullptr;
     s.exec[0] = s.exec[1] = nullptr;
@@ -1287,6 +1481,7 @@ const char *vcm_last_error(vcm_ctx *)
 
 vcm_status vcm_scene_load_mem(vcm_ctx *ctx, const float *lo, const float *hi, uint32_t n_boxes, int32_t dims)
 {
+    Range range("vcm_scene_load_mem");
     try {
         vcm_status st = validate_ctx(ctx);
         if (st != VCM_OK)
@@ -1392,6 +1587,7 @@ vcm_status vcm_scene_save(vcm_ctx *ctx, const char *path)
 
 vcm_status vcm_build(vcm_ctx *ctx, float grid_cell_m)
 {
+    Range range("vcm_build");
     try {
         vcm_status st = validate_ctx(ctx);
         if (st != VCM_OK)
@@ -1508,6 +1704,7 @@ vcm_status vcm_compute(vcm_ctx *ctx, const vcm_request *req, float *d_v, uint8_t
 vcm_status vcm_compute_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, float *const *d_v,
                              uint8_t *const *d_color, uint32_t *const *d_bits, vcm_stats *d_stats, void *stream)
 {
+    Range range("vcm_compute_batch");
     try {
         vcm_status st = validate_ctx(ctx);
         if (st != VCM_OK)
@@ -1539,6 +1736,7 @@ vcm_status vcm_compute_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, 
 
 vcm_status vcm_submit_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, uint64_t *tickets)
 {
+    Range range("vcm_submit_batch");
     try {
         vcm_status st = validate_ctx(ctx);
         if (st != VCM_OK)
@@ -1557,8 +1755,9 @@ vcm_status vcm_submit_batch(vcm_ctx *ctx, const vcm_request *reqs, uint32_t n, u
         std::lock_guard<std::mutex> g(ctx->mu);
         if (!ctx->built)
             return fail(VCM_E_STATE, "vcm_build has not been called for the current scene");
-        if (need > ctx->budget)
-            return fail(VCM_E_NOMEM, "request needs %zu bytes, budget is %zu", need, ctx->budget);
+        if (need + slot_scratch_need(ctx) > ctx->budget)
+            return fail(VCM_E_NOMEM, "request needs %zu bytes and a slot's scratch %zu, budget is %zu", need,
+                        slot_scratch_need(ctx), ctx->budget);
         const auto now = std::chrono::steady_clock::now();
         for (uint32_t i = 0; i < n; ++i) {
             auto &t = grp[i];
@@ -1631,6 +1830,10 @@ vcm_status vcm_result_get(vcm_ctx *ctx, uint64_t ticket, vcm_result *out)
     out->stats = *t.h_stats;
     out->stats.segments = (unsigned long long)t.canon.n_vp * t.canon.P;
     out->latency_ms = std::chrono::duration<double, std::milli>(t.t_done - t.t_submit).count();
+    out->queue_ms = std::chrono::duration<double, std::milli>(t.t_launch - t.t_submit).count();
+    out->device_ms = t.device_ms;
+    out->group_size = t.group_size;
+    out->launch_form = t.form;
     return VCM_OK;
 }
 
@@ -1698,7 +1901,42 @@ vcm_status vcm_set_slots(vcm_ctx *ctx, uint32_t slots, uint32_t max_batch)
     for (auto &s : ctx->slots)
         destroy_slot(*s);
     ctx->slots.clear();
+    ctx->scratch = 0;
     return start_scheduler(ctx, slots);
+}
+
+vcm_status vcm_get_memory(vcm_ctx *ctx, vcm_memory *out)
+{
+    if (!ctx || !out)
+        return fail(VCM_E_ARG, "NULL argument");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    out->budget = ctx->budget;
+    out->results = ctx->used;
+    out->slot_scratch = ctx->scratch;
+    out->slot_scratch_need = slot_scratch_need(ctx);
+    return VCM_OK;
+}
+
+vcm_status vcm_inject(vcm_ctx *ctx, uint32_t kind, uint32_t count)
+{
+    if (!ctx)
+        return fail(VCM_E_ARG, "context is NULL");
+    std::lock_guard<std::mutex> g(ctx->mu);
+    switch (kind) {
+    case VCM_INJECT_NONE:
+        if (count != 0)
+            return fail(VCM_E_ARG, "VCM_INJECT_NONE takes count 0");
+        ctx->inject_spill = ctx->inject_alloc = 0;
+        return VCM_OK;
+    case VCM_INJECT_SPILL_BUSY:
+        ctx->inject_spill = count;
+        return VCM_OK;
+    case VCM_INJECT_ALLOC_FAIL:
+        ctx->inject_alloc = count;
+        return VCM_OK;
+    default:
+        return fail(VCM_E_ARG, "unknown injection kind %u", kind);
+    }
 }
 
 vcm_status vcm_set_tune(vcm_ctx *ctx, const vcm_tune *tune)
@@ -1739,6 +1977,7 @@ vcm_status vcm_get_tune(vcm_ctx *ctx, const vcm_request *req, vcm_tune *out)
 vcm_status vcm_recolor(vcm_ctx *ctx, const vcm_request *req, const uint32_t *d_bits, float *d_v,
                        uint8_t *d_color, vcm_stats *d_stats, void *stream)
 {
+    Range range("vcm_recolor");
     try {
         vcm_status st = validate_ctx(ctx);
         if (st != VCM_OK)
@@ -1799,6 +2038,7 @@ vcm_status vcm_compute_static(const float *lo, const float *hi, uint32_t n_boxes
                               const vcm_request *req, float *d_v, uint8_t *d_color, uint32_t *d_bits,
                               vcm_stats *d_stats, void *stream)
 {
+    Range range("vcm_compute_static");
     try {
         if (dims != 2 && dims != 3)
             return fail(VCM_E_ARG, "dims must be 2 or 3");
@@ -1809,6 +2049,14 @@ vcm_status vcm_compute_static(const float *lo, const float *hi, uint32_t n_boxes
             return fail(VCM_E_ARG, "lo/hi are NULL");
         if (!d_v || !d_stats)
             return fail(VCM_E_ARG, "d_v and d_stats are required");
+        {
+            // its uploads read host memory that is freed when the call
+            // returns, so a captured copy could not be replayed
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            CUDA_TRY(cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap));
+            if (cap != cudaStreamCaptureStatusNone)
+                return fail(VCM_E_ARG, "vcm_compute_static cannot run on a stream that is being captured");
+        }
         Canon c;
         vcm_status st = canonicalise(req, c);
         if (st != VCM_OK)
@@ -1950,6 +2198,7 @@ vcm_status vcm_set_timing_events(vcm_ctx *ctx, void *before_tiles, void *after_t
 
 vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vcm_tune *out)
 {
+    Range range("vcm_autotune");
     try {
         vcm_status st = validate_ctx(ctx);
         if (st != VCM_OK)

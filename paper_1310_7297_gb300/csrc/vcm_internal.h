@@ -117,10 +117,14 @@ cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, 
 // `share` (persistent launches only): d_work is kWorkBytes long, and a second
 // launch of the kernel works the open viewpoints that expensive tiles of the
 // first published there.
+// `claim_rounds` (1..kClaimRounds) bounds the retries of a one-tile block's
+// spill-region claim; a block that gives up runs without a region and sets
+// its request's vcm_stats.error to VCM_DEVERR_SPILL_WAIT if its candidate
+// list needs one.
 cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
                          int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
                          int box_cap, bool extra, bool tile_check, cudaStream_t stream, bool one_tile = false,
-                         int *d_spill_busy = nullptr, bool share = false);
+                         int *d_spill_busy = nullptr, bool share = false, int claim_rounds = kClaimRounds);
 // Colors and edge counts for all viewpoints of n_req requests (grid over the
 // concatenated viewpoints, `d_vp_prefix` = exclusive prefix, n_req + 1).
 cudaError_t launch_quantise(const DevRequest *d_reqs, const long long *d_vp_prefix, int n_req,

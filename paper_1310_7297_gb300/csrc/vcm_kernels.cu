@@ -26,6 +26,59 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 
+// Bounds checks of the checked build (libvcm_checked, compiled with
+// VCM_CHECKED): an index outside its buffer sets the request's error word to
+// VCM_DEVERR_BOUNDS and the access is skipped; nothing traps.  In the normal
+// build the check is the constant true and costs nothing.
+#ifdef VCM_CHECKED
+__device__ __noinline__ bool in_bounds_slow(long long i, long long n, vcm_stats *st)
+{
+    if (i >= 0 && i < n)
+        return true;
+    if (st)
+        atomicExch(&st->error, (unsigned)VCM_DEVERR_BOUNDS);
+    return false;
+}
+#define IN_BOUNDS(i, n, st) in_bounds_slow((long long)(i), (long long)(n), (st))
+#else
+#define IN_BOUNDS(i, n, st) true
+#endif
+
+// Box i of a tile's candidate list: staged in shared memory, or (past
+// n_smem) through its id in the block's spill region.  The checked build
+// replaces an out-of-range id by an empty box, which blocks nothing.
+__device__ __forceinline__ void load_box(const float4 *__restrict__ sbox, int n_smem, const int *__restrict__ spill,
+                                         const float4 *__restrict__ gbox, int i, int n_boxes, vcm_stats *st,
+                                         float4 &lo, float4 &hi)
+{
+    if (i < n_smem) {
+        lo = sbox[2 * i];
+        hi = sbox[2 * i + 1];
+        return;
+    }
+    const int s = IN_BOUNDS(i - n_smem, n_boxes, st) ? spill[i - n_smem] : -1;
+    if (!IN_BOUNDS(s, n_boxes, st)) {
+        lo = make_float4(f_inf(), f_inf(), f_inf(), 0.f);
+        hi = make_float4(-f_inf(), -f_inf(), -f_inf(), 0.f);
+        return;
+    }
+    lo = __ldg(&gbox[2 * s]);
+    hi = __ldg(&gbox[2 * s + 1]);
+}
+
+// Output stores of a request: value of viewpoint vp, occlusion-bit word at
+// index `at` (bounds checked in the checked build).
+__device__ __forceinline__ void put_v(const DevRequest &R, long long vp, float v)
+{
+    if (IN_BOUNDS(vp, (long long)R.nx * R.ny * R.nl, R.stats))
+        R.v_out[vp] = v;
+}
+__device__ __forceinline__ void put_word(const DevRequest &R, long long at, uint32_t w)
+{
+    if (IN_BOUNDS(at, (long long)R.nx * R.ny * R.nl * R.words, R.stats))
+        R.bits_out[at] = w;
+}
+
 // Hardware reciprocal, at most 1 ulp from 1/d (2^-23 relative); 1/(+0) = +inf.
 // The slab-test error bound with it is about 5 u per t value, 10 u per
 // margin, still inside the 1e-6 band that is re-decided in float64.
@@ -58,32 +111,94 @@ __global__ void k_box_cell(const float *__restrict__ lo, const float *__restrict
     atomicAdd(&count[c], 1);
 }
 
-// Exclusive scan of count[0..n) into start[0..n] with one block of 1024
-// threads, each owning a contiguous chunk.
-__global__ void k_scan_exclusive(const int *__restrict__ count, int n, int *__restrict__ start)
+// Exclusive scan of count[0..n) into start[0..n] in three kernels: block
+// sums of kScanChunk elements, a one-block scan of the block sums (at most
+// 1024 of them: n <= 4M cells), then each block's scan with its offset.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;   // 4096 elements per block
+
+// Exclusive scan of one int per thread over a block of kScanThreads;
+// returns the thread's prefix and sets total.
+__device__ __forceinline__ int block_exclusive_scan(int x, int &total)
+{
+    __shared__ int s_warp[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off)
+            incl += t;
+    }
+    if (lane == 31)
+        s_warp[warp] = incl;
+    __syncthreads();
+    int before = 0;
+    total = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        before += w < warp ? s_warp[w] : 0;
+        total += s_warp[w];
+    }
+    __syncthreads();   // s_warp may be reused by the caller's next scan
+    return before + incl - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *__restrict__ count, int n,
+                                                              int *__restrict__ block_sum)
+{
+    const int base = blockIdx.x * kScanChunk;
+    int local = 0;
+    for (int i = threadIdx.x; i < kScanChunk && base + i < n; i += kScanThreads)
+        local += count[base + i];
+    int total;
+    (void)block_exclusive_scan(local, total);
+    if (threadIdx.x == 0)
+        block_sum[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the n_blocks (<= 1024) block sums in place;
+// start[n] gets the grand total.
+__global__ void __launch_bounds__(1024) k_scan_top(int *__restrict__ block_sum, int n_blocks, int n,
+                                                   int *__restrict__ start)
 {
     __shared__ int s_part[1024];
     const int t = threadIdx.x;
-    const int chunk = (n + blockDim.x - 1) / blockDim.x;
-    const int b = min(n, t * chunk), e = min(n, b + chunk);
-    int local = 0;
-    for (int i = b; i < e; ++i)
-        local += count[i];
-    s_part[t] = local;
+    const int x = t < n_blocks ? block_sum[t] : 0;
+    s_part[t] = x;
     __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        int v = (t >= off) ? s_part[t - off] : 0;
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int v = t >= off ? s_part[t - off] : 0;
         __syncthreads();
         s_part[t] += v;
         __syncthreads();
     }
-    int run = s_part[t] - local;
-    for (int i = b; i < e; ++i) {
-        start[i] = run;
-        run += count[i];
-    }
-    if (t == (int)blockDim.x - 1)
+    if (t < n_blocks)
+        block_sum[t] = s_part[t] - x;
+    if (t == 1023)
         start[n] = s_part[t];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const int *__restrict__ count, int n,
+                                                            const int *__restrict__ block_off, int *__restrict__ start)
+{
+    // each thread owns kScanItems consecutive elements of the block's chunk
+    const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    int v[kScanItems], local = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? count[base + k] : 0;
+        local += v[k];
+    }
+    int total;
+    int run = block_off[blockIdx.x] + block_exclusive_scan(local, total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n)
+            start[base + k] = run;
+        run += v[k];
+    }
 }
 
 __global__ void k_scatter(const int *__restrict__ cell_of, int n, const int *__restrict__ start,
@@ -97,21 +212,57 @@ __global__ void k_scatter(const int *__restrict__ cell_of, int n, const int *__r
     order[pos] = i;
 }
 
-// Deterministic order inside each cell: ascending original box index.
-__global__ void k_sort_cells(const int *__restrict__ start, int n_cells, int *__restrict__ order)
+// Deterministic order inside each cell: ascending box index (the scatter's
+// atomics leave it arbitrary).  Blocks take contiguous ranges of cells, a
+// thread each: a cell of at most kSmallCell boxes is sorted in place by its
+// thread; larger cells are listed, and the whole block sorts each of them by
+// rank (the rank of an id is the number of smaller ids in its cell; ids are
+// unique), writing to `tmp` (free after the scatter) and copying back.
+constexpr int kSmallCell = 32;
+
+__global__ void __launch_bounds__(kScanThreads) k_sort_cells(const int *__restrict__ start, int n_cells,
+                                                             int *__restrict__ order, int *__restrict__ tmp)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_cells)
-        return;
-    int b = start[c], e = start[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-        int v = order[i];
-        int j = i - 1;
-        while (j >= b && order[j] > v) {
-            order[j + 1] = order[j];
-            --j;
+    __shared__ int s_big[kScanThreads];
+    __shared__ int s_n_big;
+    for (int c0 = blockIdx.x * kScanThreads; c0 < n_cells; c0 += gridDim.x * kScanThreads) {
+        if (threadIdx.x == 0)
+            s_n_big = 0;
+        __syncthreads();
+        const int c = c0 + threadIdx.x;
+        if (c < n_cells) {
+            const int b = start[c], e = start[c + 1];
+            if (e - b > kSmallCell) {
+                s_big[atomicAdd(&s_n_big, 1)] = c;
+            } else {
+                for (int i = b + 1; i < e; ++i) {
+                    const int v = order[i];
+                    int j = i - 1;
+                    while (j >= b && order[j] > v) {
+                        order[j + 1] = order[j];
+                        --j;
+                    }
+                    order[j + 1] = v;
+                }
+            }
         }
-        order[j + 1] = v;
+        __syncthreads();
+        const int n_big = s_n_big;
+        for (int k = 0; k < n_big; ++k) {
+            const int cb = s_big[k];
+            const int b = start[cb], e = start[cb + 1];
+            for (int i = b + threadIdx.x; i < e; i += kScanThreads) {
+                const int v = order[i];
+                int rank = 0;
+                for (int j = b; j < e; ++j)
+                    rank += order[j] < v;
+                tmp[b + rank] = v;
+            }
+            __syncthreads();
+            for (int i = b + threadIdx.x; i < e; i += kScanThreads)
+                order[i] = tmp[i];
+            __syncthreads();
+        }
     }
 }
 
@@ -507,11 +658,12 @@ __device__ __forceinline__ bool facing(const DevRequest &R, float qn)
 }
 
 // Field-of-view cone (Section III-B, Table II): is q inside the cone of the
-// patch at q - r?  r comes in target-frame components (u, n, w), each the
-// rounded float difference q - p; the test runs in world order x, y, z with
-// one float32 rounding per operation (no fused multiply-add), exactly as the
-// request header defines it, so every implementation of that definition
-// takes the same decisions.
+// patch at q - r, a.r >= c |r|?  r comes in target-frame components
+// (u, n, w), each the rounded float difference q - p; the test runs in world
+// order x, y, z with one float32 rounding per operation (no fused
+// multiply-add), as the request header states, which errs in the margin by
+// at most about 10.5 u |r|: only pairs within 1e-6 |r| of the cone's edge
+// can be decided differently from the exact inequality.
 __device__ __forceinline__ bool in_cone_inline(const DevRequest &R, float ru, float rn, float rw)
 {
     const float r0 = R.au == 0 ? ru : (R.an == 0 ? rn : rw);
@@ -541,7 +693,8 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                                                  int n_smem, const int *__restrict__ spill, int count,
                                                  const float4 *__restrict__ gbox, float qu, float qn,
                                                  float qw, bool front, long long vp, const Plane *pyr,
-                                                 int npyr, unsigned long long &tests, unsigned &rechecks)
+                                                 int npyr, unsigned long long &tests, unsigned &rechecks,
+                                                 int n_boxes)
 {
     const int lane = threadIdx.x & 31;
     const int nuc = R.nuc, G = R.groups;
@@ -614,14 +767,7 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                     cand = true;
                 } else if (i < count) {
                     float4 lo, hi;
-                    if (i < n_smem) {
-                        lo = sbox[2 * i];
-                        hi = sbox[2 * i + 1];
-                    } else {
-                        const int s = spill[i - n_smem];
-                        lo = __ldg(&gbox[2 * s]);
-                        hi = __ldg(&gbox[2 * s + 1]);
-                    }
+                    load_box(sbox, n_smem, spill, gbox, i, n_boxes, R.stats, lo, hi);
                     cand = !outside(pyr, npyr, lo, hi);
                 }
                 todo = __ballot_sync(kFull, cand);
@@ -630,14 +776,7 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                 const int i = base + __ffs(todo) - 1;
                 todo &= todo - 1;
                 float4 lo, hi;
-                if (i < n_smem) {
-                    lo = sbox[2 * i];
-                    hi = sbox[2 * i + 1];
-                } else {
-                    const int s = spill[i - n_smem];
-                    lo = __ldg(&gbox[2 * s]);
-                    hi = __ldg(&gbox[2 * s + 1]);
-                }
+                load_box(sbox, n_smem, spill, gbox, i, n_boxes, R.stats, lo, hi);
                 const float a_u = lo.x - qu, b_u = hi.x - qu;
                 const float a_n = lo.y - qn, b_n = hi.y - qn;
                 const float tnu = (sgn_u ? a_u : b_u) * inv_u;
@@ -692,7 +831,8 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                     if (blocked) {
                         if (want_bits) {
                             const int j = iw * R.nu + iu;
-                            atomicOr(&R.bits_out[vp * R.words + (j >> 5)], 1u << (j & 31));
+                            if (IN_BOUNDS(vp * R.words + (j >> 5), (long long)R.nx * R.ny * R.nl * R.words, R.stats))
+                                atomicOr(&R.bits_out[vp * R.words + (j >> 5)], 1u << (j & 31));
                         }
                     } else if (front) {
                         // |r|^2 = (ru^2 + rn^2) of the column + rw^2 of the row
@@ -737,7 +877,8 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
 __device__ __forceinline__ float viewer_cell(const DevRequest &R, const float4 *__restrict__ sbox, int n_smem,
                                              const int *__restrict__ spill, int count,
                                              const float4 *__restrict__ gbox, float qx, float qy, float qz,
-                                             bool &blocked, unsigned long long &tests, unsigned &rechecks)
+                                             bool &blocked, unsigned long long &tests, unsigned &rechecks,
+                                             int n_boxes)
 {
     const float px = R.u_min, py = R.p_n, pz = R.w_min;
     const float dx = px - qx, dy = py - qy, dz = pz - qz;
@@ -745,14 +886,7 @@ __device__ __forceinline__ float viewer_cell(const DevRequest &R, const float4 *
     blocked = false;
     for (int i = 0; i < count && !blocked; ++i) {
         float4 lo, hi;
-        if (i < n_smem) {
-            lo = sbox[2 * i];
-            hi = sbox[2 * i + 1];
-        } else {
-            const int s = spill[i - n_smem];
-            lo = __ldg(&gbox[2 * s]);
-            hi = __ldg(&gbox[2 * s + 1]);
-        }
+        load_box(sbox, n_smem, spill, gbox, i, n_boxes, R.stats, lo, hi);
         ++tests;
         const float ax = lo.x - qx, bx = hi.x - qx, ay = lo.y - qy, by = hi.y - qy, az = lo.z - qz, bz = hi.z - qz;
         const float enter = fmaxf(fmaxf((dx >= 0.f ? ax : bx) * ix, (dy >= 0.f ? ay : by) * iy),
@@ -782,17 +916,19 @@ __device__ __forceinline__ float viewer_cell(const DevRequest &R, const float4 *
 // tile's candidate list (shared memory, then the block's spill region).
 __device__ __forceinline__ void add_candidate(const float4 *__restrict__ world, const Plane *planes, int n_planes,
                                               int s, TileSmem &sm, int *s_ids, int box_cap, int *spill,
-                                              int spill_slot, const DevRequest &R)
+                                              int spill_slot, const DevRequest &R, int n_boxes)
 {
     if (outside(planes, n_planes, world[2 * s], world[2 * s + 1]))
         return;
     const int pos = atomicAdd(&sm.count, 1);
     if (pos < box_cap)
         s_ids[pos] = s;
-    else if (spill_slot >= 0)
-        spill[pos - box_cap] = s;
-    else
-        R.stats->error = 2u;   // no spill region: the result is flagged
+    else if (spill_slot >= 0) {
+        if (IN_BOUNDS(pos - box_cap, n_boxes, R.stats))
+            spill[pos - box_cap] = s;
+    } else {
+        R.stats->error = VCM_DEVERR_SPILL_WAIT;   // no spill region: the result is flagged
+    }
 }
 
 // EXTRA: the instantiation for launches that hold a two-sided or cone
@@ -811,7 +947,7 @@ template <bool EXTRA, bool TILE_CHECK>
 __global__ void __launch_bounds__(kThreads, 5)
 k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict__ tile_prefix,
         int n_req, int total_tiles, int *__restrict__ work, int *__restrict__ spill_all, int box_cap,
-        int one_tile, int *__restrict__ spill_busy, int spill_slots, int share)
+        int one_tile, int *__restrict__ spill_busy, int spill_slots, int share, int claim_rounds)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *s_box = reinterpret_cast<float4 *>(smem_raw);
@@ -838,13 +974,14 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // claims a free region for the length of its tile.  There are as
         // many regions as blocks fit on the GPU, so a probe normally succeeds
         // at once; if every region is held (blocks of a preempted launch keep
-        // theirs), it probes again after a pause, at most kClaimRounds times
-        // (a few ms), and then runs without one and flags the result.
+        // theirs), it probes again after a pause, at most claim_rounds times
+        // (kClaimRounds by default: a few ms), and then runs without one and
+        // flags the result.
         int slot = (int)blockIdx.x;
         if (one_tile) {
             slot = -1;
             const int start = (int)(blockIdx.x % (unsigned)spill_slots);
-            for (int round = 0; round < kClaimRounds && slot < 0; ++round) {
+            for (int round = 0; round < claim_rounds && slot < 0; ++round) {
                 for (int probe = 0; probe < spill_slots && slot < 0; ++probe) {
                     const int c = (start + probe) % spill_slots;
                     if (atomicCAS(&spill_busy[c], 0, 1) == 0)
@@ -982,7 +1119,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         if (!any_front && !want_bits) {
             for (int i = tid; i < tn; i += kThreads) {
                 const int ix = ix0 + i % tw, iy = iy0 + i / tw;
-                R.v_out[((long long)layer * R.ny + iy) * R.nx + ix] = 0.f;
+                put_v(R, ((long long)layer * R.ny + iy) * R.nx + ix, 0.f);
             }
             __syncthreads();
             if (tid == 0)
@@ -1097,7 +1234,8 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                         continue;
                     }
                     for (int s = b; s < e; ++s)   // list full: this cell's boxes here
-                        add_candidate(world, sm.planes, n_planes, s, sm, s_ids, box_cap, spill, spill_slot, R);
+                        add_candidate(world, sm.planes, n_planes, s, sm, s_ids, box_cap, spill, spill_slot, R,
+                                      sc.n_boxes);
                 }
                 __syncthreads();
                 // (b) exclusive scan of the listed cells' box counts
@@ -1147,7 +1285,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                         if (s_passp[k + step] <= i)
                             k += step;
                     add_candidate(world, sm.planes, n_planes, s_passb[k] + (i - s_passp[k]), sm, s_ids, box_cap,
-                                  spill, spill_slot, R);
+                                  spill, spill_slot, R, sc.n_boxes);
                 }
                 if (tid == 0)
                     s_npass = 0;
@@ -1160,16 +1298,21 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             const int *rec = work + kWorkHeader + kRecOff + (size_t)(2 + kRecBoxes) * __ldcg(ch);
             const int cnt = __ldcg(rec + 1), n_ch = __ldcg(ch + 1);
             for (int i = tid; i < cnt; i += kThreads)
-                s_ids[i] = __ldcg(rec + 2 + i);
+                if (IN_BOUNDS(i, min(box_cap, kRecBoxes), R.stats))
+                    s_ids[i] = __ldcg(rec + 2 + i);
             for (int i = tid; i < n_ch; i += kThreads)
-                s_und[i] = __ldcg(ch + 2 + i);
+                if (IN_BOUNDS(i, kChunkVp, R.stats))
+                    s_und[i] = __ldcg(ch + 2 + i);
             if (tid == 0) {
                 sm.count = cnt;
                 sm.n_und = n_ch;
             }
         }
         __syncthreads();
-        const int count = sm.count;
+        // A block without a spill region (its bounded claim gave up) keeps
+        // only the candidates it staged: its request is already flagged
+        // (vcm_stats.error), and it reads no region it does not own.
+        const int count = spill_slot >= 0 ? sm.count : min(sm.count, box_cap);
         const int n_smem = min(count, box_cap);
         const float4 *gbox = sc.boxes[R.perm];
         // near-first order of the staged candidates: nearby boxes block the
@@ -1284,11 +1427,11 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 for (int i = tid; i < tn; i += kThreads) {
                     const int ix = ix0 + i % tw, iy = iy0 + i / tw;
                     const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
-                    R.v_out[vp] = 0.f;
+                    put_v(R, vp, 0.f);
                     if (want_bits)
                         for (int wd = 0; wd < R.words; ++wd) {
                             const int rem = R.P - 32 * wd;
-                            R.bits_out[vp * R.words + wd] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+                            put_word(R, vp * R.words + wd, rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
                         }
                 }
                 if (tid == 0)
@@ -1302,10 +1445,10 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
                 bool blocked;
                 const float v = viewer_cell(R, s_box, n_smem, spill, count, gbox, R.x_coord[ix], R.y_coord[iy],
-                                            R.dims == 3 ? zq : 0.f, blocked, tests, rechecks);
-                R.v_out[vp] = v;
+                                            R.dims == 3 ? zq : 0.f, blocked, tests, rechecks, sc.n_boxes);
+                put_v(R, vp, v);
                 if (want_bits)
-                    R.bits_out[vp] = blocked ? 1u : 0u;
+                    put_word(R, vp, blocked ? 1u : 0u);
                 vmax = fmaxf(vmax, v);
             }
         }
@@ -1344,20 +1487,23 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 const unsigned m = __ballot_sync(kFull, full);
                 const bool decided = active && ((m >> (8 * sub)) & 0xffu) != 0;
                 if (behind && bl == 0)
-                    R.v_out[vp] = 0.f;   // behind the target
+                    put_v(R, vp, 0.f);   // behind the target
                 if (decided) {
                     if (bl == 0) {
-                        R.v_out[vp] = 0.f;
+                        put_v(R, vp, 0.f);
                         ++shortcuts;
                     }
                     if (want_bits)
                         for (int wd = bl; wd < R.words; wd += 8) {
                             const int rem = R.P - 32 * wd;
-                            R.bits_out[vp * R.words + wd] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+                            put_word(R, vp * R.words + wd, rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
                         }
                 }
-                if (active && !decided && bl == 0)
-                    s_und[atomicAdd(&sm.n_und, 1)] = vi;
+                if (active && !decided && bl == 0) {
+                    const int at = atomicAdd(&sm.n_und, 1);
+                    if (IN_BOUNDS(at, kMaxTileViewpoints, R.stats))
+                        s_und[at] = vi;
+                }
             }
         }
         __syncthreads();
@@ -1428,13 +1574,13 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                         corner_tests += 4;
                     if (one_box_blocks_all(R, s_box, nb_short, qu, qn, qw)) {
                         if (lane == 0) {
-                            R.v_out[vp] = 0.f;
+                            put_v(R, vp, 0.f);
                             ++shortcuts;
                         }
                         if (want_bits)
                             for (int wd = lane; wd < R.words; wd += 32) {
                                 const int rem = R.P - 32 * wd;
-                                R.bits_out[vp * R.words + wd] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+                                put_word(R, vp * R.words + wd, rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
                             }
                         continue;
                     }
@@ -1447,17 +1593,17 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                     // sides and cone: one sweep variant of their own (8 rows
                     // per pass; the host sets k_rows = 8 for these requests)
                     v = sweep_viewpoint<8, true>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr,
-                                                 npyr, tests, rechecks);
+                                                 npyr, tests, rechecks, sc.n_boxes);
                 } else switch (R.k_rows) {
-                case 1: v = sweep_viewpoint<1, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
-                case 2: v = sweep_viewpoint<2, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
-                case 4: v = sweep_viewpoint<4, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
-                default: v = sweep_viewpoint<8, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks); break;
+                case 1: v = sweep_viewpoint<1, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
+                case 2: v = sweep_viewpoint<2, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
+                case 4: v = sweep_viewpoint<4, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
+                default: v = sweep_viewpoint<8, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
                 }
                 if (!front)
                     v = 0.f;
                 if (lane == 0)
-                    R.v_out[vp] = v;
+                    put_v(R, vp, v);
                 vmax = fmaxf(vmax, v);
             }
         }
@@ -1572,14 +1718,14 @@ __global__ void __launch_bounds__(256) k_recolor_scan(const DevRequest *__restri
                 live = !all_blocked && !(strict && any_blocked);
             }
             if (!live)
-                R.v_out[vp] = 0.f;
+                put_v(R, vp, 0.f);
         }
         const unsigned m = __ballot_sync(kFull, live);
         int at = 0;
         if (lane == 0 && m)
             at = atomicAdd(n_list, __popc(m));
         at = __shfl_sync(kFull, at, 0);
-        if (live)
+        if (live && IN_BOUNDS(at + __popc(m & ((1u << lane) - 1u)), n, R.stats))
             list[at + __popc(m & ((1u << lane) - 1u))] = (int)vp;
     }
 }
@@ -1646,7 +1792,7 @@ __global__ void __launch_bounds__(256) k_recolor_measure(const DevRequest *__res
         for (int off = 16; off > 0; off >>= 1)
             v += __shfl_xor_sync(kFull, v, off);
         if (lane == 0)
-            R.v_out[vq] = v;
+            put_v(R, vq, v);
         vmax = fmaxf(vmax, v);
     }
     if (lane == 0 && vmax > 0.f)
@@ -1684,7 +1830,7 @@ __global__ void k_quantise(const DevRequest *__restrict__ reqs, const long long 
             const float r = rintf(x);
             edge = r >= 1.f && r <= (float)(L - 2) && fabsf(x - r) <= 1e-5f * x;
         }
-        if (R.color_out)
+        if (R.color_out && IN_BOUNDS(local, (long long)R.nx * R.ny * R.nl, R.stats))
             R.color_out[local] = c;
         if (edge)   // rare; lanes of one warp may belong to different requests
             atomicAdd(&R.stats->edge_cells, 1u);
@@ -1775,10 +1921,20 @@ cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, 
     if (n > 0)
         k_box_cell<<<(n + tb - 1) / tb, tb, 0, stream>>>(d_lo_world, d_hi_world, n, gx0, gy0, 1.0f / cell,
                                                           gnx, gny, d_cell_of, d_count);
-    k_scan_exclusive<<<1, 1024, 0, stream>>>(d_count, n_cells, d_cell_start);
+    // exclusive scan of the counts; its block sums live in d_cell_lo, which
+    // k_cell_bounds writes only at the end (16 bytes per cell, 4 per block sum)
+    const int n_scan_blocks = (n_cells + kScanChunk - 1) / kScanChunk;
+    if (n_scan_blocks > 1024)
+        return cudaErrorInvalidValue;
+    int *block_sum = reinterpret_cast<int *>(d_cell_lo);
+    k_scan_reduce<<<n_scan_blocks, kScanThreads, 0, stream>>>(d_count, n_cells, block_sum);
+    k_scan_top<<<1, 1024, 0, stream>>>(block_sum, n_scan_blocks, n_cells, d_cell_start);
+    k_scan_down<<<n_scan_blocks, kScanThreads, 0, stream>>>(d_count, n_cells, block_sum, d_cell_start);
     if (n > 0) {
         k_scatter<<<(n + tb - 1) / tb, tb, 0, stream>>>(d_cell_of, n, d_cell_start, d_cursor, d_order);
-        k_sort_cells<<<(n_cells + tb - 1) / tb, tb, 0, stream>>>(d_cell_start, n_cells, d_order);
+        // d_cell_of is free after the scatter: the sort's scratch for large cells
+        const int sort_blocks = std::min((n_cells + kScanThreads - 1) / kScanThreads, 152 * 8);
+        k_sort_cells<<<sort_blocks, kScanThreads, 0, stream>>>(d_cell_start, n_cells, d_order, d_cell_of);
         PermPtrs pp;
         for (int p = 0; p < 6; ++p)
             pp.p[p] = d_perm_boxes[p];
@@ -1803,8 +1959,10 @@ int tiles_blocks_per_sm(int box_cap)
 cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int *d_tile_prefix,
                          int n_req, int total_tiles, int *d_work, int *d_spill, int grid_blocks,
                          int box_cap, bool extra, bool tile_check, cudaStream_t stream, bool one_tile,
-                         int *d_spill_busy, bool share)
+                         int *d_spill_busy, bool share, int claim_rounds)
 {
+    if (claim_rounds < 1 || claim_rounds > kClaimRounds)
+        return cudaErrorInvalidValue;
     if (total_tiles <= 0)
         return cudaSuccess;
     if (box_cap < 1 || box_cap > kMaxBoxCap)
@@ -1820,14 +1978,15 @@ cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int
                         : (tile_check ? k_tiles<false, true> : k_tiles<false, false>);
     share = share && !one_tile;
     kernel<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles, d_work, d_spill,
-                                                    box_cap, one_tile ? 1 : 0, d_spill_busy, slots, share ? 1 : 0);
+                                                    box_cap, one_tile ? 1 : 0, d_spill_busy, slots, share ? 1 : 0,
+                                                    claim_rounds);
     if (share) {
         // the second pass: the chunks the first published
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess)
             return e;
         kernel<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles, d_work,
-                                                        d_spill, box_cap, 0, d_spill_busy, slots, 2);
+                                                        d_spill, box_cap, 0, d_spill_busy, slots, 2, claim_rounds);
     }
     return cudaGetLastError();
 }

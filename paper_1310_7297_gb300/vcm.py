@@ -14,11 +14,16 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libvcm.so")
+# the same library with the kernels' bounds checks compiled in (VCM_CHECKED)
+CHECKED_LIB_PATH = os.path.join(_HERE, "_build", "libvcm_checked.so")
 
 VCM_OK, VCM_PENDING = 0, 1
 VCM_E_ARG, VCM_E_IO, VCM_E_NOMEM, VCM_E_CUDA = -1, -2, -3, -4
 VCM_E_TIMEOUT, VCM_E_CANCELLED, VCM_E_STATE = -5, -6, -7
 VCM_EMIT_BITS, VCM_STRICT, VCM_VIEWER, VCM_TWO_SIDED = 1, 2, 4, 8
+VCM_DEVERR_NONE, VCM_DEVERR_BOUNDS, VCM_DEVERR_SPILL_WAIT = 0, 1, 2
+VCM_FORM_PERSISTENT, VCM_FORM_ONE_TILE = 0, 1
+VCM_INJECT_NONE, VCM_INJECT_SPILL_BUSY, VCM_INJECT_ALLOC_FAIL = 0, 1, 2
 STATUS_NAMES = {0: "VCM_OK", 1: "VCM_PENDING", -1: "VCM_E_ARG", -2: "VCM_E_IO", -3: "VCM_E_NOMEM",
                 -4: "VCM_E_CUDA", -5: "VCM_E_TIMEOUT", -6: "VCM_E_CANCELLED", -7: "VCM_E_STATE"}
 UNITS_PER_M = 1024
@@ -28,7 +33,7 @@ EXPORTS = ["vcm_ctx_create", "vcm_ctx_destroy", "vcm_last_error", "vcm_scene_loa
            "vcm_scene_save", "vcm_build", "vcm_compute", "vcm_submit", "vcm_submit_batch", "vcm_poll",
            "vcm_result_get", "vcm_result_release", "vcm_cancel", "vcm_set_slots", "vcm_compute_batch",
            "vcm_autotune", "vcm_set_tune", "vcm_get_tune", "vcm_set_timing_events", "vcm_compute_static",
-           "vcm_recolor"]
+           "vcm_recolor", "vcm_get_memory", "vcm_inject"]
 
 
 class _DeviceArray:
@@ -68,7 +73,14 @@ class vcm_result(ctypes.Structure):
     _fields_ = [("v", ctypes.POINTER(ctypes.c_float)), ("color", ctypes.POINTER(ctypes.c_uint8)),
                 ("bits", ctypes.POINTER(ctypes.c_uint32)), ("d_v", ctypes.c_void_p),
                 ("d_color", ctypes.c_void_p), ("d_bits", ctypes.c_void_p), ("n_viewpoints", ctypes.c_uint64),
-                ("words_per_viewpoint", ctypes.c_uint32), ("stats", vcm_stats), ("latency_ms", ctypes.c_double)]
+                ("words_per_viewpoint", ctypes.c_uint32), ("stats", vcm_stats), ("latency_ms", ctypes.c_double),
+                ("queue_ms", ctypes.c_double), ("device_ms", ctypes.c_double), ("group_size", ctypes.c_uint32),
+                ("launch_form", ctypes.c_uint32)]
+
+
+class vcm_memory(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_uint64), ("results", ctypes.c_uint64), ("slot_scratch", ctypes.c_uint64),
+                ("slot_scratch_need", ctypes.c_uint64)]
 
 
 class vcm_tune(ctypes.Structure):
@@ -79,51 +91,63 @@ class vcm_tune(ctypes.Structure):
 STATS_BYTES = ctypes.sizeof(vcm_stats)
 
 _lib = None
+_lib_checked = None
 
 
-def lib():
-    """The loaded libvcm.so; raises if it has not been built."""
-    global _lib
+def lib(checked=False):
+    """The loaded libvcm.so (or libvcm_checked.so); raises if it has not
+    been built."""
+    global _lib, _lib_checked
+    if checked:
+        if _lib_checked is None:
+            _lib_checked = _load(CHECKED_LIB_PATH)
+        return _lib_checked
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libvcm.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
-        L = ctypes.CDLL(LIB_PATH)
-        P, VP, S = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int
-        L.vcm_ctx_create.argtypes = [ctypes.c_int, ctypes.c_size_t, P(VP)]
-        L.vcm_ctx_destroy.argtypes = [VP]
-        L.vcm_ctx_destroy.restype = None
-        L.vcm_last_error.argtypes = [VP]
-        L.vcm_last_error.restype = ctypes.c_char_p
-        L.vcm_scene_load_mem.argtypes = [VP, P(ctypes.c_float), P(ctypes.c_float), ctypes.c_uint32, ctypes.c_int32]
-        L.vcm_scene_load.argtypes = [VP, ctypes.c_char_p]
-        L.vcm_scene_save.argtypes = [VP, ctypes.c_char_p]
-        L.vcm_build.argtypes = [VP, ctypes.c_float]
-        L.vcm_compute.argtypes = [VP, P(vcm_request), VP, VP, VP, VP, VP]
-        L.vcm_recolor.argtypes = [VP, P(vcm_request), VP, VP, VP, VP, VP]
-        L.vcm_compute_batch.argtypes = [VP, P(vcm_request), ctypes.c_uint32, P(VP), P(VP), P(VP), VP, VP]
-        L.vcm_submit.argtypes = [VP, P(vcm_request), P(ctypes.c_uint64)]
-        L.vcm_submit_batch.argtypes = [VP, P(vcm_request), ctypes.c_uint32, P(ctypes.c_uint64)]
-        L.vcm_poll.argtypes = [VP, ctypes.c_uint64, ctypes.c_int32]
-        L.vcm_result_get.argtypes = [VP, ctypes.c_uint64, P(vcm_result)]
-        L.vcm_result_release.argtypes = [VP, ctypes.c_uint64]
-        L.vcm_cancel.argtypes = [VP, ctypes.c_uint64]
-        L.vcm_set_slots.argtypes = [VP, ctypes.c_uint32, ctypes.c_uint32]
-        L.vcm_autotune.argtypes = [VP, P(vcm_request), ctypes.c_uint32, P(vcm_tune)]
-        L.vcm_set_tune.argtypes = [VP, P(vcm_tune)]
-        L.vcm_get_tune.argtypes = [VP, P(vcm_request), P(vcm_tune)]
-        L.vcm_set_timing_events.argtypes = [VP, VP, VP]
-        L.vcm_compute_static.argtypes = [P(ctypes.c_float), P(ctypes.c_float), ctypes.c_uint32, ctypes.c_int32,
-                                         P(vcm_request), VP, VP, VP, VP, VP]
-        for name in EXPORTS:
-            if name not in ("vcm_ctx_destroy", "vcm_last_error"):
-                getattr(L, name).restype = S
-        _lib = L
+        _lib = _load(LIB_PATH)
     return _lib
 
 
-def _check(status, ctx=None):
+def _load(path):
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built; run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    P, VP, S = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int
+    L.vcm_ctx_create.argtypes = [ctypes.c_int, ctypes.c_size_t, P(VP)]
+    L.vcm_ctx_destroy.argtypes = [VP]
+    L.vcm_ctx_destroy.restype = None
+    L.vcm_last_error.argtypes = [VP]
+    L.vcm_last_error.restype = ctypes.c_char_p
+    L.vcm_scene_load_mem.argtypes = [VP, P(ctypes.c_float), P(ctypes.c_float), ctypes.c_uint32, ctypes.c_int32]
+    L.vcm_scene_load.argtypes = [VP, ctypes.c_char_p]
+    L.vcm_scene_save.argtypes = [VP, ctypes.c_char_p]
+    L.vcm_build.argtypes = [VP, ctypes.c_float]
+    L.vcm_compute.argtypes = [VP, P(vcm_request), VP, VP, VP, VP, VP]
+    L.vcm_recolor.argtypes = [VP, P(vcm_request), VP, VP, VP, VP, VP]
+    L.vcm_compute_batch.argtypes = [VP, P(vcm_request), ctypes.c_uint32, P(VP), P(VP), P(VP), VP, VP]
+    L.vcm_submit.argtypes = [VP, P(vcm_request), P(ctypes.c_uint64)]
+    L.vcm_submit_batch.argtypes = [VP, P(vcm_request), ctypes.c_uint32, P(ctypes.c_uint64)]
+    L.vcm_poll.argtypes = [VP, ctypes.c_uint64, ctypes.c_int32]
+    L.vcm_result_get.argtypes = [VP, ctypes.c_uint64, P(vcm_result)]
+    L.vcm_result_release.argtypes = [VP, ctypes.c_uint64]
+    L.vcm_cancel.argtypes = [VP, ctypes.c_uint64]
+    L.vcm_set_slots.argtypes = [VP, ctypes.c_uint32, ctypes.c_uint32]
+    L.vcm_autotune.argtypes = [VP, P(vcm_request), ctypes.c_uint32, P(vcm_tune)]
+    L.vcm_set_tune.argtypes = [VP, P(vcm_tune)]
+    L.vcm_get_tune.argtypes = [VP, P(vcm_request), P(vcm_tune)]
+    L.vcm_set_timing_events.argtypes = [VP, VP, VP]
+    L.vcm_compute_static.argtypes = [P(ctypes.c_float), P(ctypes.c_float), ctypes.c_uint32, ctypes.c_int32,
+                                     P(vcm_request), VP, VP, VP, VP, VP]
+    L.vcm_get_memory.argtypes = [VP, P(vcm_memory)]
+    L.vcm_inject.argtypes = [VP, ctypes.c_uint32, ctypes.c_uint32]
+    for name in EXPORTS:
+        if name not in ("vcm_ctx_destroy", "vcm_last_error"):
+            getattr(L, name).restype = S
+    return L
+
+
+def _check(status, ctx=None, L=None):
     if status != VCM_OK:
-        raise VcmError(status, lib().vcm_last_error(ctx).decode(errors="replace"))
+        raise VcmError(status, (L or lib()).vcm_last_error(ctx).decode(errors="replace"))
     return status
 
 
@@ -168,10 +192,12 @@ def words(d):
 class Context:
     """Owns one vcm_ctx; methods mirror the C entry points."""
 
-    def __init__(self, device=0, mem_budget_bytes=0):
-        self.L = lib()
+    def __init__(self, device=0, mem_budget_bytes=0, checked=False):
+        """checked: use libvcm_checked.so, whose kernels check their indices
+        (a failed check sets vcm_stats.error to VCM_DEVERR_BOUNDS)."""
+        self.L = lib(checked)
         h = ctypes.c_void_p()
-        _check(self.L.vcm_ctx_create(device, mem_budget_bytes, ctypes.byref(h)))
+        _check(self.L.vcm_ctx_create(device, mem_budget_bytes, ctypes.byref(h)), None, self.L)
         self.h = h
         self.device = device
 
@@ -193,7 +219,7 @@ class Context:
         self.close()
 
     def _ck(self, status):
-        return _check(status, self.h)
+        return _check(status, self.h, self.L)
 
     # scene ------------------------------------------------------------------
     def vcm_scene_load_mem(self, lo, hi, dims):
@@ -316,7 +342,8 @@ class Context:
             v, c = v.copy(), c.copy()
             b = b.copy() if b is not None else None
         st = {k: getattr(res.stats, k) for k, _ in vcm_stats._fields_}
-        st["latency_ms"] = res.latency_ms
+        for k in ("latency_ms", "queue_ms", "device_ms", "group_size", "launch_form"):
+            st[k] = getattr(res, k)
         return v, c, b, st
 
     def vcm_result_device(self, ticket):
@@ -339,7 +366,8 @@ class Context:
         # bit words as int32 (the same 32 bits; torch's uint32 support is partial)
         b = view(res.d_bits, (n, res.words_per_viewpoint), "<i4") if res.d_bits else None
         st = {k: getattr(res.stats, k) for k, _ in vcm_stats._fields_}
-        st["latency_ms"] = res.latency_ms
+        for k in ("latency_ms", "queue_ms", "device_ms", "group_size", "launch_form"):
+            st[k] = getattr(res, k)
         return v, c, b, st
 
     def vcm_result_release(self, ticket):
@@ -350,6 +378,14 @@ class Context:
 
     def vcm_set_slots(self, slots, max_batch):
         return self._ck(self.L.vcm_set_slots(self.h, slots, max_batch))
+
+    def vcm_get_memory(self):
+        m = vcm_memory()
+        self._ck(self.L.vcm_get_memory(self.h, ctypes.byref(m)))
+        return {k: getattr(m, k) for k, _ in vcm_memory._fields_}
+
+    def vcm_inject(self, kind, count):
+        return self._ck(self.L.vcm_inject(self.h, kind, count))
 
     # tuning -------------------------------------------------------------------
     def vcm_autotune(self, samples):
@@ -381,17 +417,18 @@ class Context:
         return (t.tile_x, t.tile_y, t.patch_k, t.box_cap)
 
 
-def vcm_compute_static(lo, hi, dims, req, d_v, d_color, d_bits, d_stats, stream):
+def vcm_compute_static(lo, hi, dims, req, d_v, d_color, d_bits, d_stats, stream, checked=False):
     """Module-level wrapper of the C entry point that allocates no device
     memory (no context): host boxes lo/hi (n x dims), device outputs."""
     lo = np.ascontiguousarray(np.asarray(lo, np.float32)[:, :dims])
     hi = np.ascontiguousarray(np.asarray(hi, np.float32)[:, :dims])
     r, keep = make_request(req)
     fp = ctypes.POINTER(ctypes.c_float)
-    st = lib().vcm_compute_static(lo.ctypes.data_as(fp), hi.ctypes.data_as(fp), lo.shape[0], dims, ctypes.byref(r),
-                                  d_v, d_color, d_bits, d_stats, stream)
+    L = lib(checked)
+    st = L.vcm_compute_static(lo.ctypes.data_as(fp), hi.ctypes.data_as(fp), lo.shape[0], dims, ctypes.byref(r),
+                              d_v, d_color, d_bits, d_stats, stream)
     del keep
-    return _check(st)
+    return _check(st, None, L)
 
 
 def stats_from_tensor(s):

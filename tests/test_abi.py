@@ -21,11 +21,13 @@ def test_library_builds_and_exports_every_declared_symbol():
     from paper_1310_7297_gb300 import vcm
 
     path = B.build()
-    L = ctypes.CDLL(path)
     names = declared()
     assert len(names) >= 15
-    for n in names:
-        assert hasattr(L, n), n
+    # the product library and the checked build (VCM_CHECKED) alike
+    for p in (path, B.LIB_CHECKED):
+        L = ctypes.CDLL(p)
+        for n in names:
+            assert hasattr(L, n), (p, n)
     assert sorted(vcm.EXPORTS) == names
 
 
@@ -36,7 +38,7 @@ def test_struct_layouts_match_header(tmp_path):
     from paper_1310_7297_gb300 import vcm
 
     structs = {"vcm_request": vcm.vcm_request, "vcm_stats": vcm.vcm_stats, "vcm_result": vcm.vcm_result,
-               "vcm_tune": vcm.vcm_tune}
+               "vcm_tune": vcm.vcm_tune, "vcm_memory": vcm.vcm_memory}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vcm.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))

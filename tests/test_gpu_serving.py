@@ -3,8 +3,12 @@
 Requests submitted together are merged by the scheduler into batched
 launches on several slots; each result must be the same as the request run
 alone (bit for bit: per-viewpoint sums do not depend on batching).  Memory
-admission holds requests back until the budget frees up, over-budget
-requests are refused, and queued requests can be cancelled.
+admission, which counts result buffers and the slots' scratch, holds
+requests back until the budget frees up; over-budget requests are refused,
+and queued requests can be cancelled.  Failures are made on the host
+(vcm_inject): a launch whose spill regions are all held gives up its
+bounded device-side wait and reports VCM_E_TIMEOUT; a failed buffer
+allocation reports VCM_E_NOMEM; the context keeps working after both.
 """
 
 import numpy as np
@@ -53,12 +57,22 @@ def test_mix_equals_alone(scene_reqs):
         ctx.close()
 
 
+def _slot_scratch(scene):
+    ctx = _ctx(scene)
+    try:
+        return ctx.vcm_get_memory()["slot_scratch_need"]
+    finally:
+        ctx.close()
+
+
 def test_memory_admission_and_rejection(scene_reqs):
     from paper_1310_7297_gb300 import VcmError, n_viewpoints
 
     scene, reqs = scene_reqs
     biggest = max(n_viewpoints(r) * 5 for r in reqs)
-    ctx = _ctx(scene, budget=biggest + 4096)   # room for about one request at a time
+    scratch = _slot_scratch(scene)
+    # room for one slot's scratch and about one request at a time
+    ctx = _ctx(scene, budget=scratch + biggest + 4096)
     try:
         tickets = [ctx.vcm_submit(r) for r in reqs[:8]]
         for t in tickets:
@@ -69,6 +83,96 @@ def test_memory_admission_and_rejection(scene_reqs):
         with pytest.raises(VcmError) as e:
             ctx.vcm_submit(huge)
         assert e.value.status == -3   # VCM_E_NOMEM
+        m = ctx.vcm_get_memory()
+        assert m["results"] == 0 and 0 < m["slot_scratch"] <= m["budget"]
+    finally:
+        ctx.close()
+
+
+def test_admission_counts_slot_scratch(scene_reqs):
+    """A budget that holds a request's results but not a slot's scratch
+    refuses it; one that holds both runs it."""
+    from paper_1310_7297_gb300 import VcmError, n_viewpoints
+
+    scene, reqs = scene_reqs
+    r = reqs[0]
+    need = n_viewpoints(r) * 5 + 1024
+    scratch = _slot_scratch(scene)
+    assert scratch > 13 << 20   # the work arena alone is 13 MB
+    ctx = _ctx(scene, budget=need + scratch - 1)
+    try:
+        with pytest.raises(VcmError) as e:
+            ctx.vcm_submit(r)
+        assert e.value.status == -3   # VCM_E_NOMEM
+    finally:
+        ctx.close()
+    ctx = _ctx(scene, budget=need + scratch + 4096)
+    try:
+        t = ctx.vcm_submit(r)
+        assert ctx.vcm_poll(t, -1) == 0
+        _, _, _, st = ctx.vcm_result_get(t)
+        assert st["group_size"] == 1 and st["device_ms"] > 0 and st["queue_ms"] >= 0
+        assert st["latency_ms"] >= st["queue_ms"]
+        ctx.vcm_result_release(t)
+    finally:
+        ctx.close()
+
+
+def test_bounded_spill_wait_gives_up_with_timeout(scene_reqs):
+    """Every spill region held (injected on the host) and 32 staged boxes:
+    the blocks of the launch give up their bounded claim after 8 rounds and
+    the request reports VCM_E_TIMEOUT; the next launch is complete and equals
+    the direct path."""
+    from paper_1310_7297_gb300 import VCM_INJECT_SPILL_BUSY, VcmError
+
+    # 800 boxes over 800 m: every tile's candidate list is far longer than 32
+    scene, r = synth.workload_3d(seed=7, grid=40, layers=5, patches=(32, 16), n_boxes=800, half_m=400.0,
+                                 n_components=6, sigma_m=(30.0, 120.0))
+    r = dict(r, flags=1)
+    ctx = _ctx(scene)
+    try:
+        ctx.vcm_set_tune(16, 8, 8, 32)
+        alone = gpu_run(ctx, r, bits=True)
+        assert alone[3]["boxes_listed"] > 32 * 5 * 3 * 5   # lists average more than 32
+        ctx.vcm_inject(VCM_INJECT_SPILL_BUSY, 1)
+        t = ctx.vcm_submit(r)
+        with pytest.raises(VcmError) as e:
+            ctx.vcm_poll(t, -1)
+        assert e.value.status == -5   # VCM_E_TIMEOUT
+        ctx.vcm_result_release(t)
+        t = ctx.vcm_submit(r)
+        assert ctx.vcm_poll(t, -1) == 0
+        v, c, b, st = ctx.vcm_result_get(t)
+        assert st["error"] == 0
+        assert np.array_equal(v.astype(np.float64), alone[0]) and np.array_equal(b, alone[2])
+        ctx.vcm_result_release(t)
+    finally:
+        ctx.vcm_set_tune(0)
+        ctx.close()
+
+
+def test_failed_allocation_reports_nomem_and_recovers(scene_reqs):
+    from paper_1310_7297_gb300 import VCM_INJECT_ALLOC_FAIL, VCM_INJECT_NONE, VcmError
+
+    scene, reqs = scene_reqs
+    ctx = _ctx(scene)
+    try:
+        ctx.vcm_inject(VCM_INJECT_ALLOC_FAIL, 1)
+        t = ctx.vcm_submit(reqs[2])
+        with pytest.raises(VcmError) as e:
+            ctx.vcm_poll(t, -1)
+        assert e.value.status == -3   # VCM_E_NOMEM
+        ctx.vcm_result_release(t)
+        t = ctx.vcm_submit(reqs[2])
+        assert ctx.vcm_poll(t, -1) == 0
+        ctx.vcm_result_release(t)
+        ctx.vcm_inject(VCM_INJECT_ALLOC_FAIL, 5)
+        ctx.vcm_inject(VCM_INJECT_NONE, 0)   # cleared: nothing fails
+        t = ctx.vcm_submit(reqs[2])
+        assert ctx.vcm_poll(t, -1) == 0
+        ctx.vcm_result_release(t)
+        with pytest.raises(VcmError):
+            ctx.vcm_inject(7, 1)
     finally:
         ctx.close()
 

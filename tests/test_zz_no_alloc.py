@@ -115,3 +115,55 @@ def test_static_entry_point_rejects_oversized_inputs():
                                stream)
     assert e.value.status == -1 and "65536" in str(e.value)
     torch.cuda.synchronize()
+
+
+def test_static_entry_point_near_its_box_limit_and_without_colors():
+    """4,000 boxes (box_cap 4,000: 144 KB of shared memory per block and most
+    of the array in use) agree with the context path; with d_color = NULL
+    the values still agree and nothing else is written."""
+    import torch
+
+    from paper_1310_7297_gb300 import n_viewpoints, stats_from_tensor, vcm
+
+    s, r = synth.workload_3d(seed=35, grid=48, layers=2, patches=(16, 8), n_boxes=4000, half_m=2500.0,
+                             n_components=8, sigma_m=(200.0, 800.0))
+    ref = _context(s, r, True)
+    got = _static(s, r, True)
+    assert (ref[0] > 0).sum() > 100 and ref[2].any()
+    _same(got, ref, r["color_levels"])
+    # no colors: the values and counters still come out
+    n = n_viewpoints(r)
+    v, c, b, st = _outputs(r, False)
+    c.fill_(77)
+    vcm.vcm_compute_static(s.lo_f32(), s.hi_f32(), 3, r, v.data_ptr(), None, None, st.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    compare_v(ref[0], v.cpu().numpy().astype(np.float64), "static, no colors")
+    assert (c.cpu().numpy() == 77).all()
+    assert stats_from_tensor(st)["v_ref"] == pytest.approx(ref[3]["v_ref"], rel=1e-5)
+    assert n == ref[0].shape[0]
+
+
+def test_static_entry_point_refuses_a_capturing_stream():
+    """Its uploads read host memory that is freed when the call returns, so
+    on a stream being captured into a CUDA graph it returns VCM_E_ARG
+    before enqueuing anything."""
+    import torch
+
+    from paper_1310_7297_gb300 import VcmError, vcm
+
+    s, r = synth.workload_2d(seed=36, grid=16)
+    v, c, b, st = _outputs(r, False)
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        graph.capture_begin()
+        try:
+            with pytest.raises(VcmError) as e:
+                vcm.vcm_compute_static(s.lo_f32(), s.hi_f32(), 2, r, v.data_ptr(), c.data_ptr(), None,
+                                       st.data_ptr(), side.cuda_stream)
+        finally:
+            graph.capture_end()
+    assert e.value.status == -1 and "captur" in str(e.value)
+    torch.cuda.synchronize()
