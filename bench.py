@@ -39,7 +39,7 @@ if ROOT not in sys.path:
 
 METRIC = "viewpoint-patch occlusion tests/sec and VCM cells/sec at ≤1e-5 rel err; p50/p99 latency"
 UNIT = "segments/s"
-WORKLOAD = ("3D large scene: 2048x2048 viewpoints x 8 layers, 100,000 mixture boxes over 10 km, "
+WORKLOAD = ("3D large scene: {g}x{g} viewpoints x {l} layers, 100,000 mixture boxes over 10 km, "
             "40x20 m target, 64x32 patches, 50 m grid index")
 WORKLOAD_3D = "3D plain VCM: 512x512 viewpoints x 5 layers, 5,000 mixture boxes over 2 km, 20x10 m target, 32x16 patches"
 GRID_CELL_LARGE_M = 50.0
@@ -208,10 +208,10 @@ def dist_setup():
     return world, rank, local
 
 
-def headline_workload():
+def headline_workload(grid=2048, layers=8):
     import synth
 
-    return synth.workload_3d_large()
+    return synth.workload_3d_large(grid=grid, layers=layers)
 
 
 # ---------------------------------------------------------------------------
@@ -254,7 +254,7 @@ def oracle_rate(scene, req, seconds, seed=0, rate_hint=None):
 
 def config_dict(scene, req, workload=WORKLOAD, grid_cell_m=GRID_CELL_LARGE_M):
     n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
-    return {"workload": workload, "viewpoints": n_vp, "grid": [req["grid_nx"], req["grid_ny"]],
+    return {"workload": workload.format(g=req["grid_nx"], l=len(req["layer_z"])), "viewpoints": n_vp, "grid": [req["grid_nx"], req["grid_ny"]],
             "layers_m": [z / 1024 for z in req["layer_z"]], "patches": [req["patches_u"], req["patches_w"]],
             "boxes": scene.n, "scene_digest": scene.digest(), "color_levels": req["color_levels"],
             "grid_index_cell_m": grid_cell_m,
@@ -267,7 +267,7 @@ def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    scene, req = headline_workload()
+    scene, req = headline_workload(args.grid, args.layers)
     # bounded: the whole run takes about 90 s of oracle time
     per_step = max(1.5, 90.0 / max(1, args.steps + args.warmup))
     rate = None
@@ -412,7 +412,7 @@ def run_gpu(args):
 
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    scene, req = headline_workload()
+    scene, req = headline_workload(args.grid, args.layers)
     n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
     P = req["patches_u"] * req["patches_w"]
     seg = n_vp * P
@@ -425,7 +425,7 @@ def run_gpu(args):
     time.sleep(0.3)
     K = args.steps
     head = time_direct(ctx, req, K, args.warmup, stream, flush, sampler,
-                       "the same step untimed, then the timed region", pg=pg)
+                       "the same step untimed, then the timed region", preload_s=args.preload_s, pg=pg)
     total_ms = reduce_max(float(sum(head["step_ms"])), pg, dev)
     if pg:
         pg.barrier()
@@ -527,7 +527,7 @@ def sub_3d(ctx, args, stream, flush, sampler):
     n_vp = req["grid_nx"] * req["grid_ny"] * len(req["layer_z"])
     seg = n_vp * req["patches_u"] * req["patches_w"]
     r = time_direct(ctx, req, args.steps, args.warmup, stream, flush, sampler,
-                    "the same step untimed, then the timed region")
+                    "the same step untimed, then the timed region", preload_s=args.preload_s)
     ms = float(np.mean(r["step_ms"]))
     sm_count = torch.cuda.get_device_properties(stream.device).multi_processor_count
     return {"workload": WORKLOAD_3D, "boxes": scene.n, "scene_digest": scene.digest(), "value": seg / (ms / 1e3),
@@ -722,8 +722,22 @@ def sub_serve(ctx, args, sampler):
                              "service_ms": 1e3 * (done[i] - began[i]), "segments": seg_of[i % len(pool)]}
                             for i in slow]}
 
-        # continuous batching through the scheduler
-        tickets = [None] * n
+        # continuous batching through the scheduler; a consumer thread takes
+        # each result as it is done and releases it, as a server would
+        q2 = _queue.Queue()
+        lat2, info = [0.0] * n, [None] * n
+
+        def consumer():
+            for _ in range(n):
+                i, t, ts = q2.get()
+                ctx.vcm_poll(t, -1)
+                _, hc, _, stt = ctx.vcm_result_get(t, copy=False)
+                lat2[i] = (ts - arr[i]) * 1e3 + stt["latency_ms"]
+                info[i] = {k: stt[k] for k in ("queue_ms", "device_ms", "group_size", "launch_form")}
+                ctx.vcm_result_release(t)
+
+        th2 = threading.Thread(target=consumer)
+        th2.start()
         t_w = time.monotonic()
         t0 = time.perf_counter()
         for i in range(n):
@@ -731,15 +745,9 @@ def sub_serve(ctx, args, sampler):
             if arr[i] > now:
                 time.sleep(arr[i] - now)
             ts = time.perf_counter() - t0   # the library times from here to completion
-            tickets[i] = (ctx.vcm_submit(picks[i]), ts)
-        lat2, last, info = [], 0.0, []
-        for i, (t, ts) in enumerate(tickets):
-            ctx.vcm_poll(t, -1)
-            _, hc, _, stt = ctx.vcm_result_get(t, copy=False)
-            lat2.append((ts - arr[i]) * 1e3 + stt["latency_ms"])
-            last = max(last, arr[i] + lat2[-1] / 1e3)
-            info.append({k: stt[k] for k in ("queue_ms", "device_ms", "group_size", "launch_form")})
-            ctx.vcm_result_release(t)
+            q2.put((i, ctx.vcm_submit(picks[i]), ts))
+        th2.join()
+        last = max(arr[i] + lat2[i] / 1e3 for i in range(n))
         slow = np.argsort(lat2)[-3:][::-1]
         cont = {"p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
                 "segments_per_s": seg / last, "clocks": sampler.window(t_w, time.monotonic(), "continuous arm"),
@@ -751,7 +759,7 @@ def sub_serve(ctx, args, sampler):
                                                    for i in range(n)])),
                 "slowest": [dict(latency_ms=lat2[i], segments=seg_of[i % len(pool)], **info[i]) for i in slow]}
         out.append({"rate_per_s": rate, "requests": n, "continuous": cont, "one_per_launch_fifo": fifo})
-    ctx.vcm_set_slots(4, 64)
+    ctx.vcm_set_slots(2, 64)
     return {"workload": "Poisson arrivals of requests from the batched mix against a resident 100,000-box scene",
             "unit": UNIT, "boxes": scene.n, "budget_gb": 64, "slots": args.slots, "max_batch": args.max_batch,
             "rates": out, "clocks": sampler.window(t_start, time.monotonic(), "all rates, both arms")}
@@ -1057,12 +1065,17 @@ def main():
                          "alone (batched adds the autotuner); gaze: recolouring for new gazes; equivisible: the "
                          "paper's equi-visible cells against the dense map (Eq. 6); modes: strict, field of view, "
                          "two-sided and viewer-centric variants of the 3D step")
+    ap.add_argument("--grid", type=int, default=2048,
+                    help="viewpoint grid side of the headline workload (2048; smaller only to profile a small case)")
+    ap.add_argument("--layers", type=int, default=8, help="viewpoint layers of the headline workload (8)")
+    ap.add_argument("--preload-s", type=float, default=0.6,
+                    help="seconds the step runs untimed before the timed region (for the clock samples)")
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=400)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--rates", type=float, nargs="+", default=[50, 100, 200, 500, 1000, 2000])
-    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--slots", type=int, default=2)
     ap.add_argument("--max-batch", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -188,17 +188,18 @@ typedef struct {
     vcm_stats stats;
     double latency_ms;         /* submit -> completion observed by the context */
     double queue_ms;           /* submit -> its launch began (admission and queueing) */
-    double device_ms;          /* device time of the launch that ran it (its whole group, with the
-                                  copies of results to host memory) */
+    double device_ms;          /* device time of the launch that ran it: its whole group, from its
+                                  descriptor upload to its results copied to host memory, with any
+                                  wait for the kernels of the launch before it */
     uint32_t group_size;       /* requests in that launch */
     uint32_t launch_form;      /* VCM_FORM_* of that launch */
 } vcm_result;
 
 /* How the scheduler launched a group (vcm_result.launch_form).
- * VCM_FORM_PERSISTENT: a persistent grid with the chunk pass, taken when no
- *   other request waits for a slot.
- * VCM_FORM_ONE_TILE:   one block per tile, taken while requests wait, so
- *   that launches on other slots interleave with it block by block. */
+ * VCM_FORM_PERSISTENT: a persistent grid with the chunk pass (every launch
+ *   but those of the spill-claim fault injection).
+ * VCM_FORM_ONE_TILE:   one block per tile, whose blocks claim spill regions
+ *   with a bounded wait (VCM_INJECT_SPILL_BUSY). */
 enum { VCM_FORM_PERSISTENT = 0, VCM_FORM_ONE_TILE = 1 };
 
 /* Autotuned launch shape for one class of request (see vcm_autotune). */
@@ -216,7 +217,7 @@ typedef struct {
  * (VCM_CACHE_BITS), and the scratch of the scheduler's execution slots.
  * A slot's scratch is a descriptor buffer, a spill list of n_boxes ints per
  * block that can be resident (about 304 MB per slot for 100,000 boxes on
- * 152 SMs) and a 13 MB work buffer through which the blocks of a launch
+ * 152 SMs) and a 53 MB work buffer through which the blocks of a launch
  * share the open viewpoints of expensive tiles; it is allocated when the
  * slot first runs a launch that needs it and kept.  The direct path
  * (vcm_compute, vcm_compute_batch, vcm_recolor) has scratch of its own,
@@ -269,7 +270,10 @@ vcm_status vcm_compute(vcm_ctx *ctx, const vcm_request *req, float *d_v, uint8_t
 
 /* Queue a request.  Non-blocking: a scheduler thread admits queued requests
  * as execution slots and budgeted memory free up, and runs each admitted
- * group as one batched launch while other groups are still on the device.
+ * group as one batched persistent launch while another group is still on
+ * the device: its upload and counters go at once, its kernels follow the
+ * other's back to back, and the results of one are copied while the next
+ * computes.
  * A launch whose parameters equal those of the slot's previous launch of
  * the same form is replayed from a CUDA graph captured then; others are
  * launched directly.  VCM_E_NOMEM if the request's results together with
@@ -296,8 +300,10 @@ vcm_status vcm_result_release(vcm_ctx *ctx, uint64_t ticket);
 /* Cancel a request that has not been admitted yet (VCM_E_STATE if it has). */
 vcm_status vcm_cancel(vcm_ctx *ctx, uint64_t ticket);
 
-/* Scheduler limits: number of execution slots (streams; 1..16) and the
- * largest number of requests merged into one launch. */
+/* Scheduler limits: number of execution slots (1..16; 2 by default), i.e.
+ * the launches in flight at once, each on a stream of its own, and the
+ * largest number of requests merged into one launch (64 by default).  Each
+ * slot holds scratch (see vcm_ctx_create). */
 vcm_status vcm_set_slots(vcm_ctx *ctx, uint32_t slots, uint32_t max_batch);
 
 /* Device memory of the asynchronous path, in bytes. */
@@ -340,7 +346,10 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
 /* Force a launch shape for all later launches (tile_x = 0 restores tuning). */
 vcm_status vcm_set_tune(vcm_ctx *ctx, const vcm_tune *tune);
 
-/* Launch shape the context would use for this request. */
+/* Launch shape the context would use for this request launched alone
+ * (a launch with fewer tiles than four waves of resident blocks has its
+ * tiles shrunk, 16 x 16 -> 16 x 8 -> 8 x 8 -> 8 x 4, unless a shape is
+ * forced with vcm_set_tune). */
 vcm_status vcm_get_tune(vcm_ctx *ctx, const vcm_request *req, vcm_tune *out);
 
 /* ---- without device allocation ----------------------------------------- */

@@ -345,6 +345,13 @@ void fill_shape(const Canon &c, const vcm_tune &t, DevRequest &d)
         k = 8;   // the tile kernel sweeps these requests with its 8-row variant
     d.k_rows = k;
     d.row_passes = (c.nw + d.groups * k - 1) / (d.groups * k);
+    // Work sharing: chunks of 16 open viewpoints, published from a tile
+    // with at least 8 open.  Smaller chunks for requests with many patches
+    // (about the same work per chunk) were slower: each chunk stages its
+    // owner's candidate list again (100,000-box scene, 64 x 32 patches:
+    // 8 viewpoints +7 %, 4 viewpoints +26 %; publishing from 4 open +0.5 %).
+    d.chunk_vp = kChunkVp;
+    d.min_publish = kMinPublish;
     d.tile_x = (int)std::max(1u, t.tile_x);
     d.tile_y = (int)std::max(1u, t.tile_y);
     d.tiles_x = (c.nx + d.tile_x - 1) / d.tile_x;
@@ -444,11 +451,11 @@ struct Slot {
     // lock held), then marks the in-flight group finished
     cudaEvent_t done = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr;   // device time of the in-flight launch
+    cudaEvent_t kernels_done = nullptr;       // its last kernel (before the result copies)
     std::vector<std::shared_ptr<::Ticket>> inflight;
     bool posted = false;
     std::thread waiter;
     bool scheduler = false;   // one of the scheduler's slots (its scratch counts against the budget)
-    double work = 0.0;        // segments of the in-flight group
     size_t scratch = 0;       // bytes of scratch the slot holds
     // graphs of the device work of one batched launch, one per launch form
     // (0: one block per tile, 1: persistent with the chunk pass)
@@ -516,6 +523,7 @@ struct vcm_ctx {
     bool stop = false;
     int running_groups = 0;
     size_t scratch = 0;   // scratch held by the scheduler's slots (counted against the budget)
+    Slot *last_launched = nullptr;   // the slot of the most recent scheduler launch
     // host-side fault injection (vcm_inject): launches with every spill
     // region held, and failing request-buffer allocations, still to come
     uint32_t inject_spill = 0, inject_alloc = 0;
@@ -772,6 +780,42 @@ int launch_box_cap(const std::vector<vcm_tune> &shapes)
     return (int)std::min<uint32_t>(cap, 5000);
 }
 
+// A launch with few tiles leaves SMs idle while its expensive tiles run
+// (a tile is one block's work item): shrink the tiles, 16 x 16 -> 16 x 8 ->
+// 8 x 8 -> 8 x 4, until the launch holds four waves of resident blocks.
+// Measured on the 64 requests of the serving pool, each launched alone: the
+// sum of their times 45.3 ms -> 26.1 ms (the best shape per request would
+// give 25.7 ms); a 124 x 124 x 5 grid with 64 x 32 patches 3.28 -> 0.30 ms.
+// Launches with many tiles (the 3D workloads, batches) keep their shapes.
+void shrink_small_launch(vcm_ctx *ctx, const std::vector<const Canon *> &cs, std::vector<vcm_tune> &shapes)
+{
+    if (ctx->forced || cs.empty())
+        return;
+    const long long target = 4LL * tiles_blocks_per_sm(launch_box_cap(shapes)) * ctx->sm_count;
+    for (;;) {
+        long long total = 0;
+        for (size_t i = 0; i < cs.size(); ++i) {
+            DevRequest d{};
+            fill_shape(*cs[i], shapes[i], d);
+            total += d.n_tiles;
+        }
+        if (total >= target)
+            return;
+        bool any = false;
+        for (auto &t : shapes) {
+            if (t.tile_y >= t.tile_x && t.tile_y > 4) {
+                t.tile_y /= 2;
+                any = true;
+            } else if (t.tile_x > 8) {
+                t.tile_x /= 2;
+                any = true;
+            }
+        }
+        if (!any)
+            return;
+    }
+}
+
 int grid_blocks_for(vcm_ctx *ctx, int box_cap, int total_tiles)
 {
     const int per_sm = tiles_blocks_per_sm(box_cap);
@@ -793,12 +837,16 @@ bool needs_extra(const Canon &c) { return c.cone || (c.flags & VCM_TWO_SIDED); }
 // Host half of a launch: layout, scratch, and the descriptor arena filled in
 // pinned memory.  `stats` must hold cs.size() entries.
 vcm_status prepare_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *> &cs,
-                          const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
-                          uint32_t *const *bits, vcm_stats *stats, cudaStream_t sync_stream, Prepared &P)
+                          const std::vector<vcm_tune> &shapes_in, float *const *v, uint8_t *const *color,
+                          uint32_t *const *bits, vcm_stats *stats, cudaStream_t sync_stream, Prepared &P,
+                          bool adapt = true)
 {
     Range range("vcm prepare launch");
     if (!ctx->built)
         return fail(VCM_E_STATE, "vcm_build has not been called for the current scene");
+    std::vector<vcm_tune> shapes = shapes_in;
+    if (adapt)
+        shrink_small_launch(ctx, cs, shapes);
     P.L = layout_for(cs, shapes);
     P.box_cap = launch_box_cap(shapes);
     P.blocks = grid_blocks_for(ctx, P.box_cap, P.L.total_tiles);
@@ -824,7 +872,8 @@ vcm_status prepare_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *
 // for every launch, so a captured graph can be updated in place.
 vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *stats, cudaStream_t stream,
                          bool timed = false, bool capturing = false, bool one_tile = false,
-                         int claim_rounds = kClaimRounds, bool hold_spill = false)
+                         int claim_rounds = kClaimRounds, bool hold_spill = false,
+                         cudaEvent_t after = nullptr)
 {
     Range range("vcm record launch");
     CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, P.L.bytes, cudaMemcpyHostToDevice, stream));
@@ -838,6 +887,9 @@ vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *st
     const long long *d_vps = reinterpret_cast<const long long *>(s.d_desc + P.L.off_vps);
     (void)stats;   // the descriptors point into it; the prologue clears it
     CUDA_TRY(launch_prologue(d_reqs, (int)P.n, s.d_work, P.any_bits, stream));
+    // the tile kernel starts after another launch's kernels (see launch_group)
+    if (after)
+        CUDA_TRY(cudaStreamWaitEvent(stream, after, 0));
     // fault injection: every spill region already held (any nonzero word)
     if (hold_spill)
         CUDA_TRY(cudaMemsetAsync(s.d_spill_busy, 1, s.spill_busy_cap * sizeof(int), stream));
@@ -856,10 +908,11 @@ vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *st
 
 vcm_status enqueue_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *> &cs,
                           const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
-                          uint32_t *const *bits, vcm_stats *stats, cudaStream_t stream, bool timed = false)
+                          uint32_t *const *bits, vcm_stats *stats, cudaStream_t stream, bool timed = false,
+                          bool adapt = true)
 {
     Prepared P;
-    vcm_status st = prepare_launch(ctx, s, cs, shapes, v, color, bits, stats, stream, P);
+    vcm_status st = prepare_launch(ctx, s, cs, shapes, v, color, bits, stats, stream, P, adapt);
     if (st != VCM_OK)
         return st;
     return record_launch(ctx, s, P, stats, stream, timed);
@@ -874,7 +927,7 @@ vcm_status enqueue_launch(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *
 vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *> &cs,
                          const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
                          uint32_t *const *bits, vcm_stats *stats, bool one_tile, bool direct_only = false,
-                         int claim_rounds = kClaimRounds, bool hold_spill = false)
+                         int claim_rounds = kClaimRounds, bool hold_spill = false, cudaEvent_t after = nullptr)
 {
     Prepared P;
     vcm_status st = prepare_launch(ctx, s, cs, shapes, v, color, bits, stats, s.stream, P);
@@ -892,6 +945,7 @@ vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *>
         (unsigned long long)P.blocks, P.n, (unsigned long long)P.extra, (unsigned long long)P.any_bits,
         (unsigned long long)P.tile_check, ptr(s.d_desc), ptr(s.h_desc), ptr(s.d_work), ptr(s.d_spill),
         ptr(s.d_spill_busy), ptr(stats)};
+    direct_only = direct_only || after != nullptr;   // a graph holds no wait on another stream's event
     if (!direct_only && s.exec[f] && s.key[f] == key) {
         CUDA_TRY(cudaGraphLaunch(s.exec[f], s.stream));
         CUDA_TRY(cudaEventRecord(s.desc_copied, s.stream));
@@ -900,7 +954,7 @@ vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *>
     if (direct_only || s.last_key[f] != key) {
         if (!direct_only)
             s.last_key[f] = key;
-        return record_launch(ctx, s, P, stats, s.stream, false, false, one_tile, claim_rounds, hold_spill);
+        return record_launch(ctx, s, P, stats, s.stream, false, false, one_tile, claim_rounds, hold_spill, after);
     }
     s.key[f].clear();
     CUDA_TRY(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeRelaxed));
@@ -1098,15 +1152,25 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
         bits.push_back(t->d_bits);
     }
     vcm_status st = ensure_slot(ctx, s, 0, group.size(), 1, s.stream);
-    // The persistent grid and its chunk pass on an idle GPU: a request
-    // that arrives meanwhile runs as soon as SMs free up, as it would
-    // behind a FIFO.  One block per tile while other launches run, so that
-    // they interleave block by block instead of one waiting for the other
-    // to drain.
+    // Every group gets the persistent grid and its chunk pass, and at most
+    // as many groups as there are slots are in flight (two by default).  A
+    // group launched while another is in flight uploads its descriptors and
+    // clears its counters at once, then its stream waits for the other's
+    // kernels before its tile kernel: the device runs the launches' kernels
+    // back to back with no gap for the host, the result copies of one
+    // overlap the kernels of the next, and requests that arrive meanwhile
+    // are batched into the launch after it.  Persistent grids that ran side
+    // by side starved each other's chunk pass (a request of 3.4 ms took
+    // 12 ms), and one block per tile beside other launches made a large
+    // request 2-3 times slower than alone.  One block per tile remains for
+    // the spill-claim fault injection.
     const bool inject = ctx->inject_spill > 0;
     if (inject)
         --ctx->inject_spill;
-    const bool one_tile = inject || ctx->running_groups > 0;
+    const bool one_tile = inject;
+    cudaEvent_t after = nullptr;
+    if (ctx->last_launched && ctx->last_launched != &s && ctx->last_launched->busy)
+        after = ctx->last_launched->kernels_done;
     const auto now = std::chrono::steady_clock::now();
     for (auto &t : group) {
         t->t_launch = now;
@@ -1117,7 +1181,9 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
         st = fail(VCM_E_CUDA, "cudaEventRecord failed");
     if (st == VCM_OK)
         st = enqueue_graph(ctx, s, cs, shapes, v.data(), col.data(), bits.data(), s.d_stats, one_tile,
-                           /*direct_only=*/inject, inject ? 8 : kClaimRounds, /*hold_spill=*/inject);
+                           /*direct_only=*/inject, inject ? 8 : kClaimRounds, /*hold_spill=*/inject, after);
+    if (st == VCM_OK && cudaEventRecord(s.kernels_done, s.stream) != cudaSuccess)
+        st = fail(VCM_E_CUDA, "cudaEventRecord failed");
     if (st == VCM_OK) {
         for (size_t i = 0; i < group.size(); ++i) {
             Ticket &t = *group[i];
@@ -1135,9 +1201,7 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
                 t->slot = &s;
             }
             s.inflight = group;
-            s.work = 0.0;
-            for (auto &t : group)
-                s.work += (double)t->canon.n_vp * t->canon.P;
+            ctx->last_launched = &s;
             s.posted = true;
             s.busy = true;
             ctx->running_groups++;
@@ -1208,17 +1272,6 @@ SchedStep schedule_once(vcm_ctx *ctx)
         head_need += t->canon.out_bytes() + 1024;
     }
     const bool small = head_work <= kSmallWork;
-    // A big head waits while only small groups run: they end soon, and it
-    // then gets the persistent grid on an idle GPU, which runs it faster
-    // than one block per tile beside them.
-    if (!small && ctx->running_groups > 0) {
-        double running_max = 0.0;
-        for (auto &s : ctx->slots)
-            if (s->busy)
-                running_max = std::max(running_max, s->work);
-        if (running_max <= kSmallWork)
-            return STEP_WAIT;
-    }
     const size_t scratch_need = slot_scratch_need(ctx);
     auto growth = [&](const Slot *s) { return scratch_need > s->scratch ? scratch_need - s->scratch : 0; };
     Slot *free_slot = nullptr;
@@ -1336,6 +1389,7 @@ vcm_status start_scheduler(vcm_ctx *ctx, uint32_t n_slots)
         CUDA_TRY(cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming));
         CUDA_TRY(cudaEventCreate(&s->t0));
         CUDA_TRY(cudaEventCreate(&s->t1));
+        CUDA_TRY(cudaEventCreateWithFlags(&s->kernels_done, cudaEventDisableTiming));
         s->scheduler = true;
         ctx->slots.push_back(std::move(s));
     }
@@ -1379,7 +1433,8 @@ void destroy_slot(Slot &s)
     if (s.done) cudaEventDestroy(s.done);
     if (s.t0) cudaEventDestroy(s.t0);
     if (s.t1) cudaEventDestroy(s.t1);
-    s.t0 = s.t1 = nullptr;
+    if (s.kernels_done) cudaEventDestroy(s.kernels_done);
+    s.t0 = s.t1 = s.kernels_done = nullptr;
     if (s.stream) cudaStreamDestroy(s.stream);
     s.inflight.clear();
     s.stream = nullptr;
@@ -1441,7 +1496,7 @@ vcm_status vcm_ctx_create(int device, size_t mem_budget_bytes, vcm_ctx **out)
             uint64_t thr = UINT64_MAX;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
         }
-        vcm_status st = start_scheduler(ctx.get(), 4);
+        vcm_status st = start_scheduler(ctx.get(), 2);
         if (st != VCM_OK)
             return st;
         *out = ctx.release();
@@ -1902,6 +1957,7 @@ vcm_status vcm_set_slots(vcm_ctx *ctx, uint32_t slots, uint32_t max_batch)
         destroy_slot(*s);
     ctx->slots.clear();
     ctx->scratch = 0;
+    ctx->last_launched = nullptr;
     return start_scheduler(ctx, slots);
 }
 
@@ -1967,7 +2023,9 @@ vcm_status vcm_get_tune(vcm_ctx *ctx, const vcm_request *req, vcm_tune *out)
     if (st != VCM_OK)
         return st;
     std::lock_guard<std::mutex> g(ctx->mu);
-    *out = shape_for(ctx, c);
+    std::vector<vcm_tune> shapes{shape_for(ctx, c)};
+    shrink_small_launch(ctx, {&c}, shapes);
+    *out = shapes[0];
     DevRequest d{};
     fill_shape(c, *out, d);
     out->patch_k = (uint32_t)d.k_rows;
@@ -2263,14 +2321,15 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
                 ++copies;
             }
             std::vector<float *> vv(batch.size(), d_v);   // the copies share one output (timing only)
-            vcm_status st2 = enqueue_launch(ctx, ctx->direct, batch, sh, vv.data(), nullptr, nullptr, d_stats, s);
+            vcm_status st2 = enqueue_launch(ctx, ctx->direct, batch, sh, vv.data(), nullptr, nullptr, d_stats, s,
+                                            false, /*adapt=*/false);
             if (st2 != VCM_OK)
                 return st2;
             float best_one = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 CUDA_TRY(cudaEventRecord(e0, s));
-                if ((st2 = enqueue_launch(ctx, ctx->direct, batch, sh, vv.data(), nullptr, nullptr, d_stats, s)) !=
-                    VCM_OK)
+                if ((st2 = enqueue_launch(ctx, ctx->direct, batch, sh, vv.data(), nullptr, nullptr, d_stats, s, false,
+                                          /*adapt=*/false)) != VCM_OK)
                     return st2;
                 CUDA_TRY(cudaEventRecord(e1, s));
                 CUDA_TRY(cudaEventSynchronize(e1));

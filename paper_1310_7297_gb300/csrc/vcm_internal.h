@@ -23,24 +23,34 @@ constexpr int kMaxTileViewpoints = 1024;  // viewpoints in one tile (tile_x * ti
 constexpr int kClaimRounds = 4096;        // bounded retries of a spill-region claim (2 us pauses)
 
 // Work sharing of the persistent tile kernel, in two passes.  In the first,
-// a tile whose one-box check leaves at least kMinPublish viewpoints open
-// publishes them, up to kChunkVp at a time, as chunks; the second pass (a
-// second launch of the same kernel) sweeps the chunks.  The work buffer of a
-// launch holds kWorkHeader counters (next tile, records, chunks published,
-// chunks taken) and then the arena:
-//   chunk[kChunkCap][2 + kChunkVp]       record index, count, viewpoints (tile-local)
-//   record[kRecCap][2 + kRecBoxes]       queue item, candidate count, box ids
-// A launch whose tiles would publish more than the caps keeps the rest in
-// the owning blocks.
+// a tile whose one-box check leaves at least its request's min_publish
+// viewpoints open, and whose candidate list is staged whole and holds at
+// most kPublishBoxes boxes, publishes them, chunk_vp at a time, as chunks;
+// the second pass (a second launch of the same kernel) sweeps the chunks,
+// each staging its owner's list again.
+// The work buffer of a launch holds kWorkHeader counters (next tile,
+// records, chunks published, chunks taken, id-pool ints used) and then the
+// arena:
+//   chunk[kChunkCap][2 + kChunkVp]   record index, count, viewpoints (tile-local)
+//   record[kRecCap][kRecInts]        queue item, candidate count, offset of its ids in the pool
+//   pool[kPoolInts]                  the records' candidate box ids, in the owner's order
+// A tile whose publication would pass a cap keeps its viewpoints.
 constexpr int kChunkVp = 16;
 constexpr int kMinPublish = 8;
-constexpr int kRecBoxes = 128;
-constexpr int kChunkCap = 65536;
-constexpr int kRecCap = 16384;
+// Longer lists stay with their tile (the 100,000-box scene, lists of ~180
+// boxes on average: 6.44 ms with this limit, 6.71 ms without it) unless the
+// tile has at least kPublishHeavy open viewpoints.
+constexpr int kPublishBoxes = 128;
+constexpr int kPublishHeavy = 64;
+constexpr int kChunkCap = 262144;
+constexpr int kRecCap = 65536;
+constexpr int kRecInts = 3;
+constexpr int kPoolInts = 8 << 20;
 constexpr int kWorkHeader = 64;   // ints before the arena (256 bytes)
 constexpr size_t kChunkOff = 0;
 constexpr size_t kRecOff = kChunkOff + (size_t)kChunkCap * (2 + kChunkVp);
-constexpr size_t kArenaInts = kRecOff + (size_t)kRecCap * (2 + kRecBoxes);
+constexpr size_t kPoolOff = kRecOff + (size_t)kRecCap * kRecInts;
+constexpr size_t kArenaInts = kPoolOff + (size_t)kPoolInts;
 constexpr size_t kWorkBytes = (kWorkHeader + kArenaInts) * sizeof(int);
 
 inline size_t tiles_smem_bytes(int box_cap) { return (size_t)box_cap * (32 + 4); }
@@ -75,6 +85,7 @@ struct DevRequest {
     int nx, ny, nl;            // viewpoint grid
     int tile_x, tile_y, tiles_x, tiles_y, n_tiles;
     int nuc, groups, col_passes, row_passes, k_rows;   // lane mapping
+    int chunk_vp, min_publish;   // work sharing: viewpoints per chunk, open viewpoints to publish
     const float *u_coord;      // [nu] patch centre coordinate along u
     const float *w_coord;      // [nw] along w (one 0 in 2D)
     const float *x_coord;      // [nx] viewpoint x

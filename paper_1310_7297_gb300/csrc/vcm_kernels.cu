@@ -400,7 +400,7 @@ struct TileSmem {
     int pad;
     int n_und;
     int helper;   // chunk this block took (-1: a tile from the queue)
-    int pub[3];   // record, first chunk and chunks published
+    int pub[4];   // record, first chunk, chunks published, offset of the ids in the pool
 };
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
@@ -1012,7 +1012,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             }
             if (took >= 0) {
                 const int rec = __ldcg(work + kWorkHeader + kChunkOff + (size_t)(2 + kChunkVp) * took);
-                it = __ldcg(work + kWorkHeader + kRecOff + (size_t)(2 + kRecBoxes) * rec);
+                it = __ldcg(work + kWorkHeader + kRecOff + (size_t)kRecInts * rec);
             } else if (share == 2) {
                 it = total_tiles;
             } else {
@@ -1128,6 +1128,9 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         }
 
         const int np = (R.dims == 3) ? 8 : 6;
+        // candidates past the staged ones: the block's spill region for its
+        // own tile, the record's ids in the pool for a chunk
+        const int *list_tail = spill;
         if (helper < 0) {
             hull_planes(R.dims, s_pts, np, sm);
             __syncthreads();
@@ -1295,11 +1298,12 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             // a chunk: the owner's candidate list, in the owner's order, and
             // the chunk's viewpoints
             const int *ch = work + kWorkHeader + kChunkOff + (size_t)(2 + kChunkVp) * helper;
-            const int *rec = work + kWorkHeader + kRecOff + (size_t)(2 + kRecBoxes) * __ldcg(ch);
+            const int *rec = work + kWorkHeader + kRecOff + (size_t)kRecInts * __ldcg(ch);
             const int cnt = __ldcg(rec + 1), n_ch = __ldcg(ch + 1);
-            for (int i = tid; i < cnt; i += kThreads)
-                if (IN_BOUNDS(i, min(box_cap, kRecBoxes), R.stats))
-                    s_ids[i] = __ldcg(rec + 2 + i);
+            const int *ids = work + kWorkHeader + kPoolOff + __ldcg(rec + 2);
+            for (int i = tid; i < min(cnt, box_cap); i += kThreads)
+                s_ids[i] = __ldcg(ids + i);
+            list_tail = ids + box_cap;
             for (int i = tid; i < n_ch; i += kThreads)
                 if (IN_BOUNDS(i, kChunkVp, R.stats))
                     s_und[i] = __ldcg(ch + 2 + i);
@@ -1444,7 +1448,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 const int ry = (int)(((float)vi + 0.5f) * inv_tw), ix = ix0 + vi - ry * tw, iy = iy0 + ry;
                 const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
                 bool blocked;
-                const float v = viewer_cell(R, s_box, n_smem, spill, count, gbox, R.x_coord[ix], R.y_coord[iy],
+                const float v = viewer_cell(R, s_box, n_smem, list_tail, count, gbox, R.x_coord[ix], R.y_coord[iy],
                                             R.dims == 3 ? zq : 0.f, blocked, tests, rechecks, sc.n_boxes);
                 put_v(R, vp, v);
                 if (want_bits)
@@ -1509,45 +1513,60 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         __syncthreads();
         int n_und = (viewer || tile_blocked) ? 0 : sm.n_und;
         // Work sharing, first pass (share == 1): a tile with at least
-        // kMinPublish open viewpoints publishes them, in chunks of up to
-        // kChunkVp, with its candidate list (when the list is staged whole and
-        // fits a record), and the second pass sweeps them.  Without it a few
-        // hundred tiles of mostly visible viewpoints set the end of the launch
-        // (3D workload: 100-290 us each against 17 us for the median tile).
-        // Chunks past the arena's caps stay with the tile.
-        if (share == 1 && n_und >= kMinPublish && count <= n_smem && count <= kRecBoxes) {
+        // R.min_publish open viewpoints publishes them, in chunks of up to
+        // R.chunk_vp, with its candidate list (when the list is staged
+        // whole), and the second pass sweeps them.  Without it a few hundred
+        // tiles of mostly visible viewpoints set the end of the launch (3D
+        // workload: 100-290 us each against 17 us for the median tile).  A
+        // tile with a list longer than kPublishBoxes publishes only with at
+        // least kPublishHeavy open viewpoints (each chunk stages the list
+        // again; a spilled list's tail is read from the record), and a tile
+        // whose publication would pass a cap of the arena keeps its
+        // viewpoints.
+        if (share == 1 && spill_slot >= 0 && n_und >= R.min_publish &&
+            (count <= kPublishBoxes || n_und >= kPublishHeavy)) {
             int *arena = work + kWorkHeader;
+            const int cvp = R.chunk_vp;
             if (tid == 0) {
-                const int want = (n_und + kChunkVp - 1) / kChunkVp;
-                const int rec = atomicAdd(work + 1, 1);
-                int base = 0, got = 0;
-                if (rec < kRecCap) {
-                    base = atomicAdd(work + 2, want);
-                    got = max(0, min(want, kChunkCap - base));
+                const int want = (n_und + cvp - 1) / cvp;
+                int rec = kRecCap, base = 0, got = 0, off = 0;
+                // counters move only while their caps are not reached
+                if (__ldcg(work + 1) < kRecCap && __ldcg(work + 4) < kPoolInts && __ldcg(work + 2) < kChunkCap) {
+                    rec = atomicAdd(work + 1, 1);
+                    if (rec < kRecCap) {
+                        off = atomicAdd(work + 4, count);
+                        if (off <= kPoolInts - count) {
+                            base = atomicAdd(work + 2, want);
+                            got = max(0, min(want, kChunkCap - base));
+                        }
+                    }
                 }
                 sm.pub[0] = rec;
                 sm.pub[1] = base;
                 sm.pub[2] = got;
-                s_next2 = min(n_und, got * kChunkVp);   // the tile keeps the rest
+                sm.pub[3] = off;
+                s_next2 = min(n_und, got * cvp);   // the tile keeps the rest
                 if (got > 0)
                     atomicAdd(&R.stats->shared_viewpoints, (unsigned long long)s_next2);
             }
             __syncthreads();
             const int pub_n = sm.pub[2];
             if (pub_n > 0) {
-                const int rec = sm.pub[0], pub_base = sm.pub[1];
-                int *rp = arena + kRecOff + (size_t)(2 + kRecBoxes) * rec;
+                const int rec = sm.pub[0], pub_base = sm.pub[1], off = sm.pub[3];
+                int *rp = arena + kRecOff + (size_t)kRecInts * rec;
+                int *ids = arena + kPoolOff + off;
                 if (tid == 0) {
                     rp[0] = item;
                     rp[1] = count;
+                    rp[2] = off;
                 }
                 for (int i = tid; i < count; i += kThreads)
-                    rp[2 + i] = s_ids[i];
+                    ids[i] = i < n_smem ? s_ids[i] : spill[i - n_smem];
                 for (int i = tid; i < pub_n * (2 + kChunkVp); i += kThreads) {
                     const int j = i / (2 + kChunkVp), r = i - j * (2 + kChunkVp);
-                    const int n_j = min(kChunkVp, n_und - j * kChunkVp);
+                    const int n_j = min(cvp, n_und - j * cvp);
                     arena[kChunkOff + (size_t)(2 + kChunkVp) * (pub_base + j) + r] =
-                        r == 0 ? rec : r == 1 ? n_j : (r - 2 < n_j ? s_und[j * kChunkVp + r - 2] : -1);
+                        r == 0 ? rec : r == 1 ? n_j : (r - 2 < n_j ? s_und[j * cvp + r - 2] : -1);
                 }
             }
         }
@@ -1592,13 +1611,13 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 if (EXTRA && (R.cone || (R.flags & VCM_TWO_SIDED))) {
                     // sides and cone: one sweep variant of their own (8 rows
                     // per pass; the host sets k_rows = 8 for these requests)
-                    v = sweep_viewpoint<8, true>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr,
+                    v = sweep_viewpoint<8, true>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr,
                                                  npyr, tests, rechecks, sc.n_boxes);
                 } else switch (R.k_rows) {
-                case 1: v = sweep_viewpoint<1, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
-                case 2: v = sweep_viewpoint<2, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
-                case 4: v = sweep_viewpoint<4, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
-                default: v = sweep_viewpoint<8, false>(R, s_box, n_smem, spill, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
+                case 1: v = sweep_viewpoint<1, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
+                case 2: v = sweep_viewpoint<2, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
+                case 4: v = sweep_viewpoint<4, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
+                default: v = sweep_viewpoint<8, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
                 }
                 if (!front)
                     v = 0.f;
@@ -1645,8 +1664,8 @@ __global__ void k_prologue(const DevRequest *__restrict__ reqs, int n_req, int *
 {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long nt = (long long)gridDim.x * blockDim.x;
-    if (t < 4)
-        work[t] = 0;   // next tile, records, chunks published, chunks taken
+    if (t < 5)
+        work[t] = 0;   // next tile, records, chunks published, chunks taken, id-pool ints used
     constexpr int kStatWords = (int)(sizeof(vcm_stats) / sizeof(unsigned));
     for (long long i = t; i < (long long)n_req * kStatWords; i += nt)
         reinterpret_cast<unsigned *>(reqs[i / kStatWords].stats)[i % kStatWords] = 0u;

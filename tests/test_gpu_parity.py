@@ -552,7 +552,10 @@ def test_autotune_keeps_results(ctx):
     before = [_bits_and_v(ctx, dict(r, flags=1)) for r in reqs]
     shapes = ctx.vcm_autotune(reqs)
     assert len(shapes) == len(reqs) and all(s[0] >= 1 and s[3] >= 32 for s in shapes)
-    assert ctx.vcm_get_tune(reqs[0])[:2] == shapes[0][:2]
+    # a request launched alone takes its class's shape, its tiles shrunk
+    # while the launch has few of them
+    got = ctx.vcm_get_tune(reqs[0])
+    assert got[3] == shapes[0][3] and got[0] <= shapes[0][0] and got[1] <= shapes[0][1]
     after = [_bits_and_v(ctx, dict(r, flags=1)) for r in reqs]
     for a, b in zip(before, after):
         for x, y in zip(a, b):
