@@ -88,8 +88,19 @@ enum { VCM_AXIS_PX = 0, VCM_AXIS_NX = 1, VCM_AXIS_PY = 2, VCM_AXIS_NY = 3,
  * VCM_TWO_SIDED: the target counts from both of its faces: a patch's term
  *                uses |n.(q - p)| instead of requiring n.(q - p) > 0, so
  *                viewpoints behind the target are measured too (viewpoints
- *                in its plane still get 0).  Not with VCM_VIEWER. */
-enum { VCM_EMIT_BITS = 1u, VCM_STRICT = 2u, VCM_VIEWER = 4u, VCM_TWO_SIDED = 8u };
+ *                in its plane still get 0).  Not with VCM_VIEWER.
+ * VCM_CACHE_BITS: (vcm_submit) keep the request's occlusion bits in the
+ *                context, so that a later request for the same target,
+ *                patch counts and viewpoint grid (scene unchanged) that
+ *                differs only in field of view, gaze, sides, strictness,
+ *                color levels or v_ref is served from them by recolouring,
+ *                with no occlusion test (Section IV-C: when the gaze turns,
+ *                the work done for every direction is reused).  The bits
+ *                count against the budget; the least recently used are
+ *                dropped when admission needs the memory, and all when the
+ *                scene changes.  Ignored by the direct calls; not with
+ *                VCM_VIEWER. */
+enum { VCM_EMIT_BITS = 1u, VCM_STRICT = 2u, VCM_VIEWER = 4u, VCM_TWO_SIDED = 8u, VCM_CACHE_BITS = 16u };
 
 #define VCM_UNITS_PER_M 1024
 #define VCM_COORD_LIMIT_M 16384.0f
@@ -120,7 +131,7 @@ typedef struct {
     const float *layer_z;    /* host pointer, n_layers heights; copied */
     uint32_t color_levels;   /* L, 2..256 */
     float v_ref;             /* > 0: normalise by this; <= 0: by the largest v */
-    uint32_t flags;          /* VCM_EMIT_BITS | VCM_STRICT | VCM_VIEWER | VCM_TWO_SIDED */
+    uint32_t flags;          /* VCM_EMIT_BITS | VCM_STRICT | VCM_VIEWER | VCM_TWO_SIDED | VCM_CACHE_BITS */
     /* Field of view of the target (Section III-B: the visible region starts
      * as the part of space inside the FOV, 120 degrees by default in
      * Table II; Section IV-C turns the gaze).  fov_deg in (0, 360): patch p
@@ -197,10 +208,12 @@ typedef struct {
 
 /* How the scheduler launched a group (vcm_result.launch_form).
  * VCM_FORM_PERSISTENT: a persistent grid with the chunk pass (every launch
- *   but those of the spill-claim fault injection).
+ *   but those below).
  * VCM_FORM_ONE_TILE:   one block per tile, whose blocks claim spill regions
- *   with a bounded wait (VCM_INJECT_SPILL_BUSY). */
-enum { VCM_FORM_PERSISTENT = 0, VCM_FORM_ONE_TILE = 1 };
+ *   with a bounded wait (VCM_INJECT_SPILL_BUSY).
+ * VCM_FORM_RECOLOR:    recoloured from occlusion bits cached by an earlier
+ *   request (VCM_CACHE_BITS); stats.slab_tests and corner_tests are 0. */
+enum { VCM_FORM_PERSISTENT = 0, VCM_FORM_ONE_TILE = 1, VCM_FORM_RECOLOR = 2 };
 
 /* Autotuned launch shape for one class of request (see vcm_autotune). */
 typedef struct {
@@ -313,8 +326,14 @@ typedef struct {
     uint64_t slot_scratch;       /* scratch the scheduler's slots hold now */
     uint64_t slot_scratch_need;  /* scratch one slot needs for the current scene (counted
                                     against the budget before a slot first runs) */
+    uint64_t cached_bits;        /* occlusion bits kept for recolouring (VCM_CACHE_BITS) */
+    uint32_t cache_entries;
 } vcm_memory;
 vcm_status vcm_get_memory(vcm_ctx *ctx, vcm_memory *out);
+
+/* Drop the occlusion bits kept for recolouring (VCM_CACHE_BITS) that no
+ * running request uses. */
+vcm_status vcm_cache_clear(vcm_ctx *ctx);
 
 /* Host-side fault injection, for testing how failures surface (nothing
  * here faults or stalls the GPU).

@@ -7,7 +7,7 @@ include/vcm.h); ``vcm`` is its thin ctypes binding.  Build it with
 """
 
 from .vcm import (  # noqa: F401
-    VCM_DEVERR_BOUNDS, VCM_DEVERR_NONE, VCM_DEVERR_SPILL_WAIT, VCM_EMIT_BITS, VCM_FORM_ONE_TILE,
-    VCM_FORM_PERSISTENT, VCM_INJECT_ALLOC_FAIL, VCM_INJECT_NONE, VCM_INJECT_SPILL_BUSY, VCM_STRICT,
+    VCM_CACHE_BITS, VCM_DEVERR_BOUNDS, VCM_DEVERR_NONE, VCM_DEVERR_SPILL_WAIT, VCM_EMIT_BITS, VCM_FORM_ONE_TILE,
+    VCM_FORM_PERSISTENT, VCM_FORM_RECOLOR, VCM_INJECT_ALLOC_FAIL, VCM_INJECT_NONE, VCM_INJECT_SPILL_BUSY, VCM_STRICT,
     VCM_TWO_SIDED, VCM_VIEWER, Context, VcmError, lib, make_request, n_viewpoints, stats_from_tensor, words,
 )

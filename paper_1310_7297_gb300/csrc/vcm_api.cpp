@@ -170,8 +170,10 @@ vcm_status canonicalise(const vcm_request *r, Canon &c)
     if (r->dims != 2 && r->dims != 3)
         return fail(VCM_E_ARG, "dims must be 2 or 3 (got %d)", r->dims);
     c.dims = r->dims;
-    if (r->flags & ~(uint32_t)(VCM_EMIT_BITS | VCM_STRICT | VCM_VIEWER | VCM_TWO_SIDED))
+    if (r->flags & ~(uint32_t)(VCM_EMIT_BITS | VCM_STRICT | VCM_VIEWER | VCM_TWO_SIDED | VCM_CACHE_BITS))
         return fail(VCM_E_ARG, "unknown flag bits 0x%x", r->flags);
+    if ((r->flags & VCM_CACHE_BITS) && (r->flags & VCM_VIEWER))
+        return fail(VCM_E_ARG, "VCM_CACHE_BITS and VCM_VIEWER exclude each other");
     if ((r->flags & VCM_STRICT) && (r->flags & VCM_VIEWER))
         return fail(VCM_E_ARG, "VCM_STRICT and VCM_VIEWER exclude each other");
     if ((r->flags & VCM_TWO_SIDED) && (r->flags & VCM_VIEWER))
@@ -476,6 +478,20 @@ struct Layout {
     long long total_vp;
 };
 
+// Occlusion bits kept for recolouring (VCM_CACHE_BITS): a request's bits
+// do not depend on its field of view, gaze, sides, strictness or colours,
+// so a later request whose canonical target, patches and viewpoint grid are
+// the same (scene unchanged) is served from them (Section IV-C).
+struct CacheEntry {
+    std::vector<float> key;        // canonical geometry (cache_key)
+    unsigned long long scene_gen = 0;
+    uint32_t *d_bits = nullptr;
+    size_t bytes = 0;
+    bool ready = false;            // the launch that fills it has completed
+    int users = 0;                 // in-flight launches writing or reading it
+    uint64_t last_use = 0;
+};
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -527,6 +543,10 @@ struct vcm_ctx {
     // host-side fault injection (vcm_inject): launches with every spill
     // region held, and failing request-buffer allocations, still to come
     uint32_t inject_spill = 0, inject_alloc = 0;
+    // occlusion bits kept for recolouring, least recently used first out
+    std::vector<std::shared_ptr<CacheEntry>> cache;
+    size_t cache_bytes = 0;
+    uint64_t cache_clock = 0;
 };
 
 namespace {
@@ -554,6 +574,8 @@ struct Ticket {
     std::chrono::steady_clock::time_point t_submit, t_launch, t_done;
     double device_ms = 0.0;
     uint32_t group_size = 0, form = 0;
+    std::shared_ptr<CacheEntry> cache_fill;   // cached bits this request's launch writes
+    std::shared_ptr<CacheEntry> cache_hit;    // cached bits it is recoloured from
 };
 
 namespace {
@@ -1030,6 +1052,70 @@ bool scheduler_idle(vcm_ctx *ctx) { return ctx->queue.empty() && ctx->running_gr
 // scheduler
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// occlusion bits kept for recolouring (VCM_CACHE_BITS)
+// ---------------------------------------------------------------------------
+
+// The canonical geometry that fixes a request's occlusion bits: the
+// normal's axis, side and coordinate, the patch centres and the viewpoint
+// grid.  Field of view, gaze, sides, strictness and colours are left out.
+std::vector<float> cache_key(const Canon &c)
+{
+    std::vector<float> k = {(float)c.dims, (float)c.au, (float)c.an, (float)c.aw, c.sn, c.p_n,
+                            (float)c.nu, (float)c.nw, (float)c.nx, (float)c.ny, (float)c.nl};
+    for (const std::vector<float> *v : {&c.u_coord, &c.w_coord, &c.x_coord, &c.y_coord, &c.z_coord})
+        k.insert(k.end(), v->begin(), v->end());
+    return k;
+}
+
+size_t bits_bytes(const Canon &c) { return (size_t)c.n_vp * c.words * sizeof(uint32_t); }
+
+// A request the recolour kernels can serve (their viewpoint list is int).
+bool cacheable(const Canon &c) { return !(c.flags & VCM_VIEWER) && c.n_vp <= (long long)INT32_MAX; }
+
+std::shared_ptr<CacheEntry> cache_find(vcm_ctx *ctx, const Canon &c, bool ready_only)
+{
+    if (ctx->cache.empty() || !cacheable(c))
+        return nullptr;
+    const std::vector<float> key = cache_key(c);
+    for (auto &e : ctx->cache)
+        if (e->scene_gen == ctx->scene_gen && (e->ready || !ready_only) && e->key == key)
+            return e;
+    return nullptr;
+}
+
+void cache_drop(vcm_ctx *ctx, const std::shared_ptr<CacheEntry> &e)
+{
+    auto it = std::find(ctx->cache.begin(), ctx->cache.end(), e);
+    if (it == ctx->cache.end())
+        return;
+    if (e->d_bits)
+        cudaFreeAsync(e->d_bits, ctx->aux);
+    e->d_bits = nullptr;
+    ctx->cache_bytes -= e->bytes;
+    ctx->cache.erase(it);
+}
+
+// Drop the least recently used entry that no launch uses; false if none.
+bool cache_evict_one(vcm_ctx *ctx)
+{
+    std::shared_ptr<CacheEntry> victim;
+    for (auto &e : ctx->cache)
+        if (e->users == 0 && (!victim || e->last_use < victim->last_use))
+            victim = e;
+    if (!victim)
+        return false;
+    cache_drop(ctx, victim);
+    return true;
+}
+
+// Drop every entry no launch uses (all of them when nothing runs).
+void cache_clear(vcm_ctx *ctx)
+{
+    while (cache_evict_one(ctx)) {
+    }
+}
+
 // Completion of a slot's launches.  CUDA host callbacks are not used: a
 // callback that takes the context lock can deadlock against a thread that
 // holds the lock inside a call that implicitly synchronises the device
@@ -1075,6 +1161,18 @@ void slot_waiter(vcm_ctx *ctx, Slot *s)
                 t->state = T_DONE;
             }
             t->t_done = now;
+            if (t->cache_fill) {   // the bits are there once the launch has run cleanly
+                auto e = t->cache_fill;
+                e->users--;
+                e->ready = t->state == T_DONE;
+                if (!e->ready && e->users == 0)
+                    cache_drop(ctx, e);
+                t->cache_fill.reset();
+            }
+            if (t->cache_hit) {
+                t->cache_hit->users--;
+                t->cache_hit.reset();
+            }
         }
         s->busy = false;
         ctx->running_groups--;
@@ -1144,12 +1242,22 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
     std::vector<float *> v;
     std::vector<uint8_t *> col;
     std::vector<uint32_t *> bits;
-    for (auto &t : group) {
-        cs.push_back(&t->canon);
+    // a request that fills cached bits emits them into the cache's buffer
+    std::vector<Canon> filling(group.size());
+    for (size_t i = 0; i < group.size(); ++i) {
+        auto &t = group[i];
+        if (t->cache_fill) {
+            filling[i] = t->canon;
+            filling[i].flags |= VCM_EMIT_BITS;
+            cs.push_back(&filling[i]);
+            bits.push_back(t->cache_fill->d_bits);
+        } else {
+            cs.push_back(&t->canon);
+            bits.push_back(t->d_bits);
+        }
         shapes.push_back(t->shape);
         v.push_back(t->d_v);
         col.push_back(t->d_color);
-        bits.push_back(t->d_bits);
     }
     vcm_status st = ensure_slot(ctx, s, 0, group.size(), 1, s.stream);
     // Every group gets the persistent grid and its chunk pass, and at most
@@ -1188,6 +1296,8 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
         for (size_t i = 0; i < group.size(); ++i) {
             Ticket &t = *group[i];
             const Canon &c = t.canon;
+            if (t.cache_fill && t.d_bits)   // the caller asked for the bits too
+                cudaMemcpyAsync(t.d_bits, t.cache_fill->d_bits, bits_bytes(c), cudaMemcpyDeviceToDevice, s.stream);
             cudaMemcpyAsync(t.h_v, t.d_v, (size_t)c.n_vp * 4, cudaMemcpyDeviceToHost, s.stream);
             cudaMemcpyAsync(t.h_color, t.d_color, (size_t)c.n_vp, cudaMemcpyDeviceToHost, s.stream);
             if (t.d_bits)
@@ -1210,12 +1320,91 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
         st = fail(VCM_E_CUDA, "cudaEventRecord failed");
     }
     for (auto &t : group) {
+        if (t->cache_fill) {
+            t->cache_fill->users--;
+            cache_drop(ctx, t->cache_fill);
+            t->cache_fill.reset();
+        }
         t->state = T_ERROR;
         t->err = st;
         t->msg = t_err;
         t->t_done = std::chrono::steady_clock::now();
         release_buffers(ctx, *t);
     }
+}
+
+// Launch one request served from cached occlusion bits (ctx->mu held): its
+// descriptor, the recolour kernels (Section IV-C: the field of view, gaze,
+// sides and strictness applied to bits made earlier), colours, and the
+// copies of its results, chained after the launch in flight like any other.
+void launch_recolor_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &group)
+{
+    Range range("vcm launch recolour");
+    Ticket &t = *group[0];
+    const std::shared_ptr<CacheEntry> e = t.cache_hit;
+    Canon c = t.canon;
+    c.flags &= ~(unsigned)(VCM_EMIT_BITS | VCM_CACHE_BITS);   // the bits are an input here
+    const std::vector<const Canon *> cs{&c};
+    const std::vector<vcm_tune> shapes{default_tune()};
+    const Layout L = layout_for(cs, shapes);
+    cudaEvent_t after = nullptr;
+    if (ctx->last_launched && ctx->last_launched != &s && ctx->last_launched->busy)
+        after = ctx->last_launched->kernels_done;
+    t.t_launch = std::chrono::steady_clock::now();
+    t.group_size = 1;
+    t.form = VCM_FORM_RECOLOR;
+    vcm_status st = ensure_slot(ctx, s, L.bytes, 1, 1, s.stream);
+    auto body = [&]() -> vcm_status {
+        CUDA_TRY(cudaEventSynchronize(s.desc_copied));
+        float *vv[1] = {t.d_v};
+        uint8_t *cc[1] = {t.d_color};
+        uint32_t *bb[1] = {e->d_bits};   // read only in k_recolor
+        fill_desc(s.h_desc, s.d_desc, L, cs, shapes, vv, cc, bb, s.d_stats, 256);
+        CUDA_TRY(cudaEventRecord(s.t0, s.stream));
+        CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, L.bytes, cudaMemcpyHostToDevice, s.stream));
+        CUDA_TRY(cudaEventRecord(s.desc_copied, s.stream));
+        CUDA_TRY(cudaMemsetAsync(s.d_stats, 0, sizeof(vcm_stats), s.stream));
+        if (after)
+            CUDA_TRY(cudaStreamWaitEvent(s.stream, after, 0));
+        const DevRequest *d_reqs = reinterpret_cast<const DevRequest *>(s.d_desc + L.off_reqs);
+        const long long *d_vps = reinterpret_cast<const long long *>(s.d_desc + L.off_vps);
+        int *list = nullptr;   // the viewpoints that need a measure, and their count
+        CUDA_TRY(cudaMallocAsync((void **)&list, sizeof(int) * ((size_t)c.n_vp + 1), s.stream));
+        const cudaError_t le = launch_recolor(d_reqs, c.n_vp, ctx->sm_count, list, list + c.n_vp, s.stream);
+        cudaFreeAsync(list, s.stream);
+        CUDA_TRY(le);
+        CUDA_TRY(launch_quantise(d_reqs, d_vps, 1, c.n_vp, s.stream));
+        CUDA_TRY(cudaEventRecord(s.kernels_done, s.stream));
+        CUDA_TRY(cudaMemcpyAsync(t.h_v, t.d_v, (size_t)c.n_vp * 4, cudaMemcpyDeviceToHost, s.stream));
+        CUDA_TRY(cudaMemcpyAsync(t.h_color, t.d_color, (size_t)c.n_vp, cudaMemcpyDeviceToHost, s.stream));
+        if (t.d_bits) {
+            CUDA_TRY(cudaMemcpyAsync(t.d_bits, e->d_bits, bits_bytes(c), cudaMemcpyDeviceToDevice, s.stream));
+            CUDA_TRY(cudaMemcpyAsync(t.h_bits, e->d_bits, bits_bytes(c), cudaMemcpyDeviceToHost, s.stream));
+        }
+        CUDA_TRY(cudaMemcpyAsync(t.h_stats, s.d_stats, sizeof(vcm_stats), cudaMemcpyDeviceToHost, s.stream));
+        CUDA_TRY(cudaEventRecord(s.t1, s.stream));
+        CUDA_TRY(cudaEventRecord(s.done, s.stream));
+        return VCM_OK;
+    };
+    if (st == VCM_OK)
+        st = body();
+    if (st == VCM_OK) {
+        t.state = T_RUNNING;
+        t.slot = &s;
+        s.inflight = group;
+        ctx->last_launched = &s;
+        s.posted = true;
+        s.busy = true;
+        ctx->running_groups++;
+        return;
+    }
+    e->users--;
+    t.cache_hit.reset();
+    t.state = T_ERROR;
+    t.err = st;
+    t.msg = t_err;
+    t.t_done = std::chrono::steady_clock::now();
+    release_buffers(ctx, t);
 }
 
 enum SchedStep { STEP_WAIT, STEP_LAUNCHED, STEP_PROGRESS };
@@ -1274,6 +1463,7 @@ SchedStep schedule_once(vcm_ctx *ctx)
     const bool small = head_work <= kSmallWork;
     const size_t scratch_need = slot_scratch_need(ctx);
     auto growth = [&](const Slot *s) { return scratch_need > s->scratch ? scratch_need - s->scratch : 0; };
+    const size_t held = ctx->used + ctx->scratch + ctx->cache_bytes;   // charged against the budget
     Slot *free_slot = nullptr;
     bool any_free = false;
     for (int trimmed = 0; trimmed < 2 && !free_slot; ++trimmed) {
@@ -1283,7 +1473,7 @@ SchedStep schedule_once(vcm_ctx *ctx)
             for (auto &s : ctx->slots)
                 if (!s->busy && (pass == 1 || s->high_priority == small)) {
                     any_free = true;
-                    if (ctx->used + ctx->scratch + growth(s.get()) + head_need <= ctx->budget) {
+                    if (held + growth(s.get()) + head_need <= ctx->budget) {
                         free_slot = s.get();
                         break;
                     }
@@ -1304,24 +1494,36 @@ SchedStep schedule_once(vcm_ctx *ctx)
         return STEP_WAIT;   // finished results still hold memory until released
     // admit groups from the front of the queue while memory allows
     std::vector<std::shared_ptr<Ticket>> batch;
-    bool alloc_failed = false;
+    bool alloc_failed = false, recolour = false;
     double batch_work = 0.0;
     const size_t slot_growth = growth(free_slot);
     while (!ctx->queue.empty()) {
         auto &grp = ctx->queue.front();
-        size_t need = 0;
+        // a request whose bits are cached runs alone, as a recolour
+        std::shared_ptr<CacheEntry> hit = grp.size() == 1 ? cache_find(ctx, grp[0]->canon, true) : nullptr;
+        if (hit && !batch.empty())
+            break;
+        size_t need = 0, fill = 0;
         double work = 0.0;
         for (auto &t : grp) {
             need += t->canon.out_bytes() + 1024;
             work += (double)t->canon.n_vp * t->canon.P;
+            if (!hit && (t->canon.flags & VCM_CACHE_BITS) && cacheable(t->canon) && !cache_find(ctx, t->canon, false))
+                fill += bits_bytes(t->canon);
         }
+        if (hit)
+            need += sizeof(int) * ((size_t)grp[0]->canon.n_vp + 1);   // the recolour's viewpoint list
         if (!batch.empty() && batch.size() + grp.size() > ctx->max_batch)
             break;
         // a batch completes as a whole: keep small requests out of big batches
         if (!batch.empty() && batch_work + work > kBatchWork)
             break;
-        if (ctx->used + ctx->scratch + slot_growth + need > ctx->budget)
+        if (ctx->used + ctx->scratch + ctx->cache_bytes + slot_growth + need + fill > ctx->budget) {
+            // cached bits nobody uses give way to admitted work
+            if (cache_evict_one(ctx))
+                continue;
             break;
+        }
         bool ok = true;
         for (auto &t : grp) {
             if (!alloc_buffers(ctx, *t, free_slot->stream)) {
@@ -1337,10 +1539,35 @@ SchedStep schedule_once(vcm_ctx *ctx)
             alloc_failed = true;
             break;
         }
-        for (auto &t : grp)
+        for (auto &t : grp) {
+            if (hit) {
+                t->cache_hit = hit;
+                hit->users++;
+                hit->last_use = ++ctx->cache_clock;
+            } else if ((t->canon.flags & VCM_CACHE_BITS) && cacheable(t->canon) && !cache_find(ctx, t->canon, false)) {
+                // this launch fills the cache (a failed allocation only skips caching)
+                auto e = std::make_shared<CacheEntry>();
+                e->key = cache_key(t->canon);
+                e->scene_gen = ctx->scene_gen;
+                e->bytes = bits_bytes(t->canon);
+                if (cudaMallocAsync((void **)&e->d_bits, e->bytes, free_slot->stream) == cudaSuccess) {
+                    e->users = 1;
+                    e->last_use = ++ctx->cache_clock;
+                    ctx->cache.push_back(e);
+                    ctx->cache_bytes += e->bytes;
+                    t->cache_fill = e;
+                } else {
+                    cudaGetLastError();
+                }
+            }
             batch.push_back(t);
+        }
         batch_work += work;
         ctx->queue.pop_front();
+        if (hit) {
+            recolour = true;
+            break;
+        }
     }
     if (batch.empty()) {
         // Only a device allocation that fails with nothing in flight is
@@ -1358,7 +1585,10 @@ SchedStep schedule_once(vcm_ctx *ctx)
         }
         return STEP_WAIT;
     }
-    launch_group(ctx, *free_slot, batch);
+    if (recolour)
+        launch_recolor_group(ctx, *free_slot, batch);
+    else
+        launch_group(ctx, *free_slot, batch);
     return STEP_LAUNCHED;
 }
 
@@ -1518,6 +1748,9 @@ void vcm_ctx_destroy(vcm_ctx *ctx)
         for (auto &kv : ctx->tickets)
             release_buffers(ctx, *kv.second);
         ctx->tickets.clear();
+        for (auto &e : ctx->cache)
+            e->users = 0;   // nothing runs any more
+        cache_clear(ctx);
     }
     cudaStreamSynchronize(ctx->aux);
     for (auto &s : ctx->slots)
@@ -1564,6 +1797,7 @@ vcm_status vcm_scene_load_mem(vcm_ctx *ctx, const float *lo, const float *hi, ui
             return fail(VCM_E_STATE, "requests are still queued or running");
         // work still reading the old scene must finish before it is replaced
         CUDA_TRY(cudaDeviceSynchronize());
+        cache_clear(ctx);   // cached bits belong to the old scene
         ctx->built = false;
         ctx->dims = dims;
         ctx->n_boxes = n_boxes;
@@ -1680,6 +1914,7 @@ vcm_status vcm_build(vcm_ctx *ctx, float grid_cell_m)
         const int n_cells = gnx * gny;
         // work still reading the old index must finish before it is rebuilt
         CUDA_TRY(cudaDeviceSynchronize());
+        cache_clear(ctx);   // cached bits belong to the old index's scene
         ctx->built = false;
         const size_t nb = std::max<uint32_t>(n, 1);
         if (nb > ctx->idx_box_cap) {   // index buffers are reused while large enough
@@ -1970,6 +2205,21 @@ vcm_status vcm_get_memory(vcm_ctx *ctx, vcm_memory *out)
     out->results = ctx->used;
     out->slot_scratch = ctx->scratch;
     out->slot_scratch_need = slot_scratch_need(ctx);
+    out->cached_bits = ctx->cache_bytes;
+    out->cache_entries = (uint32_t)ctx->cache.size();
+    return VCM_OK;
+}
+
+vcm_status vcm_cache_clear(vcm_ctx *ctx)
+{
+    vcm_status st = validate_ctx(ctx);
+    if (st != VCM_OK)
+        return st;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        cache_clear(ctx);
+    }
+    ctx->cv.notify_all();   // freed memory may admit queued requests
     return VCM_OK;
 }
 

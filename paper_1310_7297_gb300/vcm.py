@@ -20,9 +20,9 @@ CHECKED_LIB_PATH = os.path.join(_HERE, "_build", "libvcm_checked.so")
 VCM_OK, VCM_PENDING = 0, 1
 VCM_E_ARG, VCM_E_IO, VCM_E_NOMEM, VCM_E_CUDA = -1, -2, -3, -4
 VCM_E_TIMEOUT, VCM_E_CANCELLED, VCM_E_STATE = -5, -6, -7
-VCM_EMIT_BITS, VCM_STRICT, VCM_VIEWER, VCM_TWO_SIDED = 1, 2, 4, 8
+VCM_EMIT_BITS, VCM_STRICT, VCM_VIEWER, VCM_TWO_SIDED, VCM_CACHE_BITS = 1, 2, 4, 8, 16
 VCM_DEVERR_NONE, VCM_DEVERR_BOUNDS, VCM_DEVERR_SPILL_WAIT = 0, 1, 2
-VCM_FORM_PERSISTENT, VCM_FORM_ONE_TILE = 0, 1
+VCM_FORM_PERSISTENT, VCM_FORM_ONE_TILE, VCM_FORM_RECOLOR = 0, 1, 2
 VCM_INJECT_NONE, VCM_INJECT_SPILL_BUSY, VCM_INJECT_ALLOC_FAIL = 0, 1, 2
 STATUS_NAMES = {0: "VCM_OK", 1: "VCM_PENDING", -1: "VCM_E_ARG", -2: "VCM_E_IO", -3: "VCM_E_NOMEM",
                 -4: "VCM_E_CUDA", -5: "VCM_E_TIMEOUT", -6: "VCM_E_CANCELLED", -7: "VCM_E_STATE"}
@@ -33,7 +33,7 @@ EXPORTS = ["vcm_ctx_create", "vcm_ctx_destroy", "vcm_last_error", "vcm_scene_loa
            "vcm_scene_save", "vcm_build", "vcm_compute", "vcm_submit", "vcm_submit_batch", "vcm_poll",
            "vcm_result_get", "vcm_result_release", "vcm_cancel", "vcm_set_slots", "vcm_compute_batch",
            "vcm_autotune", "vcm_set_tune", "vcm_get_tune", "vcm_set_timing_events", "vcm_compute_static",
-           "vcm_recolor", "vcm_get_memory", "vcm_inject"]
+           "vcm_recolor", "vcm_get_memory", "vcm_inject", "vcm_cache_clear"]
 
 
 class _DeviceArray:
@@ -80,7 +80,8 @@ class vcm_result(ctypes.Structure):
 
 class vcm_memory(ctypes.Structure):
     _fields_ = [("budget", ctypes.c_uint64), ("results", ctypes.c_uint64), ("slot_scratch", ctypes.c_uint64),
-                ("slot_scratch_need", ctypes.c_uint64)]
+                ("slot_scratch_need", ctypes.c_uint64), ("cached_bits", ctypes.c_uint64),
+                ("cache_entries", ctypes.c_uint32)]
 
 
 class vcm_tune(ctypes.Structure):
@@ -139,6 +140,7 @@ def _load(path):
                                      P(vcm_request), VP, VP, VP, VP, VP]
     L.vcm_get_memory.argtypes = [VP, P(vcm_memory)]
     L.vcm_inject.argtypes = [VP, ctypes.c_uint32, ctypes.c_uint32]
+    L.vcm_cache_clear.argtypes = [VP]
     for name in EXPORTS:
         if name not in ("vcm_ctx_destroy", "vcm_last_error"):
             getattr(L, name).restype = S
@@ -386,6 +388,9 @@ class Context:
 
     def vcm_inject(self, kind, count):
         return self._ck(self.L.vcm_inject(self.h, kind, count))
+
+    def vcm_cache_clear(self):
+        return self._ck(self.L.vcm_cache_clear(self.h))
 
     # tuning -------------------------------------------------------------------
     def vcm_autotune(self, samples):

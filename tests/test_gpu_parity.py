@@ -378,7 +378,7 @@ def test_argument_errors(ctx):
     ctx.compute(dict(req, center=[1, 0, 0]))     # one lattice unit off centre is fine
     for r, st in [(dict(req, dims=4), -1), (dict(req, normal=0), -1), (dict(req, color_levels=1), -1),
                   (dict(req, grid_step=[0, 8000]), -1), (dict(req, patches_u=0), -1),
-                  (dict(req, flags=16), -1)]:
+                  (dict(req, flags=32), -1), (dict(req, flags=16 | 4), -1)]:
         with pytest.raises(VcmError) as e:
             ctx.compute(r)
         assert e.value.status == st

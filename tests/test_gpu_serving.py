@@ -220,3 +220,65 @@ def test_scheduler_spill_path_matches_direct(scene_reqs):
     finally:
         ctx.vcm_set_tune(0)
         ctx.close()
+
+
+def test_gaze_change_is_served_from_cached_bits(scene_reqs):
+    """Incremental processing in the server (Section IV-C): a request with
+    VCM_CACHE_BITS leaves its occlusion bits in the context; later requests
+    for the same target and grid with another field of view, gaze, sides,
+    strictness or colours are served by recolouring those bits (launch form
+    VCM_FORM_RECOLOR, no slab test), and each equals a fresh vcm_compute of
+    the same request.  The bits are counted in the memory report, freed by
+    vcm_cache_clear, and dropped when the index is rebuilt."""
+    from gpu_util import device_edge_cells
+    from paper_1310_7297_gb300 import (VCM_CACHE_BITS, VCM_EMIT_BITS, VCM_FORM_RECOLOR, VCM_STRICT, VCM_TWO_SIDED,
+                                       n_viewpoints, words)
+
+    scene, reqs = scene_reqs
+    ctx = _ctx(scene)
+    try:
+        r = max(reqs[:8], key=n_viewpoints)
+        t = ctx.vcm_submit(dict(r, flags=VCM_CACHE_BITS))
+        assert ctx.vcm_poll(t, -1) == 0
+        v0, _, _, st0 = ctx.vcm_result_get(t)
+        assert st0["launch_form"] != VCM_FORM_RECOLOR and st0["slab_tests"] + st0["corner_tests"] > 0
+        ctx.vcm_result_release(t)
+        ref0, _, _, _ = gpu_run(ctx, r, bits=False)
+        assert np.array_equal(v0.astype(np.float64), ref0)
+        m = ctx.vcm_get_memory()
+        assert m["cache_entries"] == 1 and m["cached_bits"] == n_viewpoints(r) * words(r) * 4
+        cases = [dict(fov_deg=120.0), dict(fov_deg=90.0, gaze=[0.5, 1.0, 0.0]), dict(flags=VCM_TWO_SIDED),
+                 dict(flags=VCM_STRICT, fov_deg=150.0), dict(color_levels=5, v_ref=0.3), dict(flags=VCM_EMIT_BITS)]
+        for extra in cases:
+            q = dict(r, **extra)
+            t = ctx.vcm_submit(q)
+            assert ctx.vcm_poll(t, -1) == 0
+            v, c, b, st = ctx.vcm_result_get(t)
+            ctx.vcm_result_release(t)
+            assert st["launch_form"] == VCM_FORM_RECOLOR and st["slab_tests"] == 0 and st["error"] == 0, extra
+            bits = bool(q.get("flags", 0) & VCM_EMIT_BITS)
+            dv, dc, db, dst = gpu_run(ctx, q, bits=bits)
+            v = v.astype(np.float64)
+            assert np.array_equal(v == 0, dv == 0) and np.allclose(v, dv, rtol=2e-6, atol=0), extra
+            L = q["color_levels"]
+            edge = device_edge_cells(v, st["v_ref"], L) | device_edge_cells(dv, dst["v_ref"], L)
+            assert ((c == dc) | edge).all(), extra
+            if bits:
+                assert np.array_equal(b, db)
+        # another grid is computed, not recoloured
+        other = dict(r, grid_nx=r["grid_nx"] - 1)
+        t = ctx.vcm_submit(other)
+        assert ctx.vcm_poll(t, -1) == 0
+        assert ctx.vcm_result_get(t)[3]["launch_form"] != VCM_FORM_RECOLOR
+        ctx.vcm_result_release(t)
+        ctx.vcm_cache_clear()
+        assert ctx.vcm_get_memory()["cache_entries"] == 0
+        t = ctx.vcm_submit(dict(r, flags=VCM_CACHE_BITS))
+        assert ctx.vcm_poll(t, -1) == 0
+        ctx.vcm_result_release(t)
+        assert ctx.vcm_get_memory()["cache_entries"] == 1
+        ctx.vcm_build(50.0)   # a new index: the cached bits belong to the old one
+        m = ctx.vcm_get_memory()
+        assert m["cache_entries"] == 0 and m["cached_bits"] == 0
+    finally:
+        ctx.close()
