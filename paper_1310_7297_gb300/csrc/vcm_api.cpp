@@ -476,6 +476,7 @@ struct Layout {
     size_t off_reqs, off_tiles, off_vps, off_coords, bytes;
     int total_tiles;
     long long total_vp;
+    long long blocker_ints;   // tile positions of the requests in the blocker table
 };
 
 // Occlusion bits kept for recolouring (VCM_CACHE_BITS): a request's bits
@@ -623,12 +624,16 @@ Layout layout_for(const std::vector<const Canon *> &cs, const std::vector<vcm_tu
     size_t coords = 0;
     L.total_tiles = 0;
     L.total_vp = 0;
+    L.blocker_ints = 0;
     for (size_t i = 0; i < n; ++i) {
         coords += cs[i]->coord_count();
         DevRequest d{};
         fill_shape(*cs[i], shapes[i], d);
         L.total_tiles += d.n_tiles;
         L.total_vp += cs[i]->n_vp;
+        const long long pos = (long long)d.tiles_x * d.tiles_y;
+        if (L.blocker_ints + pos <= kBlockerCap)   // fill_desc gives the same offsets
+            L.blocker_ints += pos;
     }
     L.bytes = align_up(L.off_coords + sizeof(float) * coords, 256);
     return L;
@@ -637,7 +642,7 @@ Layout layout_for(const std::vector<const Canon *> &cs, const std::vector<vcm_tu
 // Fill the pinned descriptor arena (host side) for a launch.
 void fill_desc(char *h, const char *d_base, const Layout &L, const std::vector<const Canon *> &cs,
                const std::vector<vcm_tune> &shapes, float *const *v, uint8_t *const *color,
-               uint32_t *const *bits, vcm_stats *stats, int box_cap)
+               uint32_t *const *bits, vcm_stats *stats, int box_cap, bool blockers = true)
 {
     const size_t n = cs.size();
     DevRequest *reqs = reinterpret_cast<DevRequest *>(h + L.off_reqs);
@@ -647,7 +652,7 @@ void fill_desc(char *h, const char *d_base, const Layout &L, const std::vector<c
     const float *d_coords = reinterpret_cast<const float *>(d_base + L.off_coords);
     size_t at = 0;
     int tp = 0;
-    long long vp = 0;
+    long long vp = 0, blk = 0;
     for (size_t i = 0; i < n; ++i) {
         const Canon &c = *cs[i];
         DevRequest d{};
@@ -682,6 +687,14 @@ void fill_desc(char *h, const char *d_base, const Layout &L, const std::vector<c
         d.cone_c = c.cone_c;
         for (int k = 0; k < 3; ++k)
             d.cone_a[k] = c.cone_a[k];
+        // the request's tile positions in the blocker table (as layout_for counts them)
+        d.blk_base = -1;
+        const long long pos = (long long)d.tiles_x * d.tiles_y;
+        if (blk + pos <= kBlockerCap) {
+            if (blockers)
+                d.blk_base = (int)blk;
+            blk += pos;
+        }
         reqs[i] = d;
         tiles[i] = tp;
         vps[i] = vp;
@@ -909,6 +922,9 @@ vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *st
     const long long *d_vps = reinterpret_cast<const long long *>(s.d_desc + P.L.off_vps);
     (void)stats;   // the descriptors point into it; the prologue clears it
     CUDA_TRY(launch_prologue(d_reqs, (int)P.n, s.d_work, P.any_bits, stream));
+    if (P.tile_check && P.L.blocker_ints > 0)   // no blocker recorded yet (-1)
+        CUDA_TRY(cudaMemsetAsync(s.d_work + kWorkHeader + kBlockerOff, 0xFF, (size_t)P.L.blocker_ints * sizeof(int),
+                                 stream));
     // the tile kernel starts after another launch's kernels (see launch_group)
     if (after)
         CUDA_TRY(cudaStreamWaitEvent(stream, after, 0));
@@ -1359,7 +1375,7 @@ void launch_recolor_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Tic
         float *vv[1] = {t.d_v};
         uint8_t *cc[1] = {t.d_color};
         uint32_t *bb[1] = {e->d_bits};   // read only in k_recolor
-        fill_desc(s.h_desc, s.d_desc, L, cs, shapes, vv, cc, bb, s.d_stats, 256);
+        fill_desc(s.h_desc, s.d_desc, L, cs, shapes, vv, cc, bb, s.d_stats, 256, /*blockers=*/false);
         CUDA_TRY(cudaEventRecord(s.t0, s.stream));
         CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, L.bytes, cudaMemcpyHostToDevice, s.stream));
         CUDA_TRY(cudaEventRecord(s.desc_copied, s.stream));
@@ -2324,7 +2340,7 @@ vcm_status vcm_recolor(vcm_ctx *ctx, const vcm_request *req, const uint32_t *d_b
         float *vv[1] = {d_v};
         uint8_t *cc[1] = {d_color};
         uint32_t *bb[1] = {const_cast<uint32_t *>(d_bits)};   // read only in k_recolor
-        fill_desc(s.h_desc, s.d_desc, L, cs, shapes, vv, cc, bb, d_stats, 256);
+        fill_desc(s.h_desc, s.d_desc, L, cs, shapes, vv, cc, bb, d_stats, 256, /*blockers=*/false);
         CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, L.bytes, cudaMemcpyHostToDevice, strm));
         CUDA_TRY(cudaEventRecord(s.desc_copied, strm));
         CUDA_TRY(cudaMemsetAsync(d_stats, 0, sizeof(vcm_stats), strm));
@@ -2473,7 +2489,7 @@ vcm_status vcm_compute_static(const float *lo, const float *hi, uint32_t n_boxes
         float *vv[1] = {d_v};
         uint8_t *cc[1] = {d_color};
         uint32_t *bb[1] = {d_bits};
-        fill_desc(hdesc.data(), s_desc, lay, cs, shapes, vv, cc, bb, d_stats, (int)t.box_cap);
+        fill_desc(hdesc.data(), s_desc, lay, cs, shapes, vv, cc, bb, d_stats, (int)t.box_cap, /*blockers=*/false);
         CUDA_TRY(cudaMemcpyAsync(s_desc, hdesc.data(), lay.bytes, cudaMemcpyHostToDevice, sm));
         const DevRequest *d_reqs = reinterpret_cast<const DevRequest *>(s_desc + lay.off_reqs);
         const int *d_tiles = reinterpret_cast<const int *>(s_desc + lay.off_tiles);

@@ -34,6 +34,8 @@ constexpr int kClaimRounds = 4096;        // bounded retries of a spill-region c
 //   chunk[kChunkCap][2 + kChunkVp]   record index, count, viewpoints (tile-local)
 //   record[kRecCap][kRecInts]        queue item, candidate count, offset of its ids in the pool
 //   pool[kPoolInts]                  the records' candidate box ids, in the owner's order
+//   blocker[kBlockerCap]             per tile position of each request (whole-tile-check
+//                                    launches): a box id that blocked a tile there, or -1
 // A tile whose publication would pass a cap keeps its viewpoints.
 constexpr int kChunkVp = 16;
 constexpr int kMinPublish = 8;
@@ -46,11 +48,13 @@ constexpr int kChunkCap = 262144;
 constexpr int kRecCap = 65536;
 constexpr int kRecInts = 3;
 constexpr int kPoolInts = 8 << 20;
+constexpr int kBlockerCap = 1 << 20;
 constexpr int kWorkHeader = 64;   // ints before the arena (256 bytes)
 constexpr size_t kChunkOff = 0;
 constexpr size_t kRecOff = kChunkOff + (size_t)kChunkCap * (2 + kChunkVp);
 constexpr size_t kPoolOff = kRecOff + (size_t)kRecCap * kRecInts;
-constexpr size_t kArenaInts = kPoolOff + (size_t)kPoolInts;
+constexpr size_t kBlockerOff = kPoolOff + (size_t)kPoolInts;
+constexpr size_t kArenaInts = kBlockerOff + (size_t)kBlockerCap;
 constexpr size_t kWorkBytes = (kWorkHeader + kArenaInts) * sizeof(int);
 
 inline size_t tiles_smem_bytes(int box_cap) { return (size_t)box_cap * (32 + 4); }
@@ -86,6 +90,7 @@ struct DevRequest {
     int tile_x, tile_y, tiles_x, tiles_y, n_tiles;
     int nuc, groups, col_passes, row_passes, k_rows;   // lane mapping
     int chunk_vp, min_publish;   // work sharing: viewpoints per chunk, open viewpoints to publish
+    int blk_base;                // offset of its tile positions in the blocker table, or -1
     const float *u_coord;      // [nu] patch centre coordinate along u
     const float *w_coord;      // [nw] along w (one 0 in 2D)
     const float *x_coord;      // [nx] viewpoint x

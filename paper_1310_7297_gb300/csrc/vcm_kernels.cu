@@ -1127,11 +1127,42 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             continue;
         }
 
+        // Whole-tile shortcut from recorded blockers (launches with the
+        // whole-tile check): a box that blocked this tile position on
+        // another layer, or a neighbouring position, often blocks this tile
+        // too, so threads 0-4 test those first, against the same 16
+        // segments as the check below; a tile one of them blocks skips its
+        // cull.  Any tile writes the table, so which blocker it keeps is a
+        // race; a box counts only if it certainly blocks, so results do not
+        // depend on the table.
+        int *blockers = work + kWorkHeader + kBlockerOff;
+        const int tile_pos = ty * R.tiles_x + tx;
+        bool pre_blocked = false;
+        unsigned long long pre_tests = 0;
+        if (TILE_CHECK && !viewer && helper < 0 && R.blk_base >= 0) {
+            bool full = false;
+            if (tid < 5) {
+                const int px = tx + (tid == 1) - (tid == 2), py = ty + (tid == 3) - (tid == 4);
+                const int cand = (px >= 0 && px < R.tiles_x && py >= 0 && py < R.tiles_y)
+                                     ? __ldcg(blockers + R.blk_base + py * R.tiles_x + px)
+                                     : -1;
+                if (cand >= 0 && cand < sc.n_boxes) {
+                    const float4 *gb = sc.boxes[R.perm];
+                    full = box_blocks_tile(R, __ldg(&gb[2 * cand]), __ldg(&gb[2 * cand + 1]), R.x_coord[ix0],
+                                           R.x_coord[ix1 - 1], R.y_coord[iy0], R.y_coord[iy1 - 1], zq);
+                    pre_tests = 16;
+                    if (full && tid != 0)
+                        blockers[R.blk_base + tile_pos] = cand;
+                }
+            }
+            pre_blocked = __syncthreads_or(full) != 0;
+        }
+
         const int np = (R.dims == 3) ? 8 : 6;
         // candidates past the staged ones: the block's spill region for its
         // own tile, the record's ids in the pool for a chunk
         const int *list_tail = spill;
-        if (helper < 0) {
+        if (helper < 0 && !pre_blocked) {
             hull_planes(R.dims, s_pts, np, sm);
             __syncthreads();
         }
@@ -1147,7 +1178,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // is spanned by the interval's two ends.  Rows are taken 128 at a
         // time: one thread finds a row's span, a block scan lays the spans
         // end to end, and the threads share out the cells.
-        if (helper < 0) {
+        if (helper < 0 && !pre_blocked) {
             float ax0 = s_pts[0][0], ax1 = ax0, ay0 = s_pts[0][1], ay1 = ay0;
             for (int l = 1; l < 4; ++l) {
                 ax0 = fminf(ax0, s_pts[l][0]); ax1 = fmaxf(ax1, s_pts[l][0]);
@@ -1294,7 +1325,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                     s_npass = 0;
                 __syncthreads();   // the next rows reuse the span arrays
             }
-        } else {
+        } else if (helper >= 0) {
             // a chunk: the owner's candidate list, in the owner's order, and
             // the chunk's viewpoints
             const int *ch = work + kWorkHeader + kChunkOff + (size_t)(2 + kChunkVp) * helper;
@@ -1418,29 +1449,32 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // it from the whole tile rectangle; the one-box argument over the
         // target plane then covers every patch of every viewpoint.  Threads
         // take the nearest candidates, one each, against all 16 segments.
-        bool tile_blocked = false;
-        if (TILE_CHECK && !viewer && helper < 0) {
+        bool tile_blocked = pre_blocked;
+        corner_tests += pre_tests;
+        if (TILE_CHECK && !viewer && helper < 0 && !pre_blocked) {
             bool full = false;
             if (tid < min(n_smem, kThreads)) {
                 full = box_blocks_tile(R, s_box[2 * tid], s_box[2 * tid + 1], R.x_coord[ix0], R.x_coord[ix1 - 1],
                                        R.y_coord[iy0], R.y_coord[iy1 - 1], zq);
                 corner_tests += 16;
+                if (full && R.blk_base >= 0)   // for the tiles of this position and its neighbours
+                    blockers[R.blk_base + tile_pos] = s_ids[tid];
             }
             tile_blocked = __syncthreads_or(full) != 0;
-            if (tile_blocked) {
-                for (int i = tid; i < tn; i += kThreads) {
-                    const int ix = ix0 + i % tw, iy = iy0 + i / tw;
-                    const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
-                    put_v(R, vp, 0.f);
-                    if (want_bits)
-                        for (int wd = 0; wd < R.words; ++wd) {
-                            const int rem = R.P - 32 * wd;
-                            put_word(R, vp * R.words + wd, rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
-                        }
-                }
-                if (tid == 0)
-                    shortcuts += (unsigned)tn;
+        }
+        if (tile_blocked) {
+            for (int i = tid; i < tn; i += kThreads) {
+                const int ix = ix0 + i % tw, iy = iy0 + i / tw;
+                const long long vp = ((long long)layer * R.ny + iy) * R.nx + ix;
+                put_v(R, vp, 0.f);
+                if (want_bits)
+                    for (int wd = 0; wd < R.words; ++wd) {
+                        const int rem = R.P - 32 * wd;
+                        put_word(R, vp * R.words + wd, rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u));
+                    }
             }
+            if (tid == 0)
+                shortcuts += (unsigned)tn;
         }
         if (viewer) {
             // viewer-centric: threads take cells, one segment each
