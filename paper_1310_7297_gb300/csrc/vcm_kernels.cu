@@ -580,24 +580,26 @@ __device__ __forceinline__ bool one_box_blocks_all(const DevRequest &R, const fl
     return __any_sync(kFull, full);
 }
 
-// Planes of the pyramid with apex q and base the rectangle of extreme patch
-// centres (2D: the triangle q, segment ends), in the target frame (u, n, w).
-// Every segment from q to a patch centre lies in it, so a box outside one of
-// the planes meets none of them.  Each plane's offset is the largest float32
+// Planes of the pyramid with apex q and base the rectangle [u_lo, u_hi] x
+// [w_lo, w_hi] of patch centres (2D: the triangle q, segment ends), in the
+// target frame (u, n, w).  Every segment from q to a patch centre in the
+// rectangle lies in it, so a box outside one of the planes meets none of
+// them.  Each plane's offset is the largest float32
 // evaluation over all the pyramid's points plus the same margin as the tile
 // hull, so the half-space holds the whole pyramid whatever the plane's
 // orientation; a degenerate plane only culls less.  Lanes 0..5 each write
 // one plane (NaN-free: degenerate normals are dropped); returns the count.
 // Not inlined: each sweep variant would carry a copy (1 % on the 3D step).
-__device__ __noinline__ int pyramid_planes(const DevRequest &R, float qu, float qn, float qw, Plane *out)
+__device__ __noinline__ int pyramid_planes(const DevRequest &R, float qu, float qn, float qw, float u_lo, float u_hi,
+                                           float w_lo, float w_hi, Plane *out)
 {
     const int lane = threadIdx.x & 31;
     // rectangle corners in order (u_min,w_min) (u_max,w_min) (u_max,w_max) (u_min,w_max)
     const float P[5][3] = {{qu, qn, qw},
-                           {R.u_min, R.p_n, R.w_min},
-                           {R.u_max, R.p_n, R.w_min},
-                           {R.u_max, R.p_n, R.w_max},
-                           {R.u_min, R.p_n, R.w_max}};
+                           {u_lo, R.p_n, w_lo},
+                           {u_hi, R.p_n, w_lo},
+                           {u_hi, R.p_n, w_hi},
+                           {u_lo, R.p_n, w_hi}};
     float nx = 0.f, ny = 0.f, nz = 0.f;
     bool ok = false;
     if (lane == 0) {
@@ -606,8 +608,8 @@ __device__ __noinline__ int pyramid_planes(const DevRequest &R, float qu, float 
         ok = R.p_n != qn;
     } else if (lane <= 4) {
         const int e = lane - 1, f = lane & 3;   // rectangle edge e -> f
-        const float eu = (e == 0 || e == 3) ? R.u_min : R.u_max, ew = (e < 2) ? R.w_min : R.w_max;
-        const float fu = (f == 0 || f == 3) ? R.u_min : R.u_max, fw = (f < 2) ? R.w_min : R.w_max;
+        const float eu = (e == 0 || e == 3) ? u_lo : u_hi, ew = (e < 2) ? w_lo : w_hi;
+        const float fu = (f == 0 || f == 3) ? u_lo : u_hi, fw = (f < 2) ? w_lo : w_hi;
         if (R.dims == 3) {
             const float ax = eu - qu, ay = R.p_n - qn, az = ew - qw;
             const float bx = fu - qu, by = R.p_n - qn, bz = fw - qw;
@@ -624,8 +626,8 @@ __device__ __noinline__ int pyramid_planes(const DevRequest &R, float qu, float 
         if (ok) {
             nx /= len; ny /= len; nz /= len;
             // outward: away from a point inside the pyramid
-            const float cu = 0.5f * (qu + 0.5f * (R.u_min + R.u_max)), cn = 0.5f * (qn + R.p_n);
-            const float cw = 0.5f * (qw + 0.5f * (R.w_min + R.w_max));
+            const float cu = 0.5f * (qu + 0.5f * (u_lo + u_hi)), cn = 0.5f * (qn + R.p_n);
+            const float cw = 0.5f * (qw + 0.5f * (w_lo + w_hi));
             if (dot3(nx, ny, nz, cu, cn, cw) > dot3(nx, ny, nz, qu, qn, qw)) {
                 nx = -nx; ny = -ny; nz = -nz;
             }
@@ -692,8 +694,8 @@ template <int K, bool EXTRA>
 __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const float4 *__restrict__ sbox,
                                                  int n_smem, const int *__restrict__ spill, int count,
                                                  const float4 *__restrict__ gbox, float qu, float qn,
-                                                 float qw, bool front, long long vp, const Plane *pyr,
-                                                 int npyr, unsigned long long &tests, unsigned &rechecks,
+                                                 float qw, bool front, long long vp, Plane *pyr,
+                                                 bool use_pyr, unsigned long long &tests, unsigned &rechecks,
                                                  int n_boxes)
 {
     const int lane = threadIdx.x & 31;
@@ -754,6 +756,18 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
             unsigned alive = valid;
             if (!__any_sync(kFull, alive != 0))
                 continue;
+            // The pyramid filter for this pass: apex q, base the rectangle
+            // of the patch centres the pass covers (its columns by its rows),
+            // so a box whose shadow misses them is dropped before its rows
+            // are tested.
+            int npyr = 0;
+            if (use_pyr) {
+                const int c0 = cp * nuc, c1 = min(R.nu, c0 + nuc) - 1;
+                const int r0 = rp * K * G, r1 = min(R.nw, r0 + K * G) - 1;
+                const float ua = R.u_coord[c0], ub = R.u_coord[c1], wa = w_coord[r0], wb = w_coord[r1];
+                __syncwarp();   // the previous pass has done with the planes
+                npyr = pyramid_planes(R, qu, qn, qw, fminf(ua, ub), fmaxf(ua, ub), fminf(wa, wb), fmaxf(wa, wb), pyr);
+            }
             int nb = 0;
             bool done = false;
             for (int base = 0; base < count && !done; base += 32) {
@@ -1139,7 +1153,8 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         const int tile_pos = ty * R.tiles_x + tx;
         bool pre_blocked = false;
         unsigned long long pre_tests = 0;
-        if (TILE_CHECK && !viewer && helper < 0 && R.blk_base >= 0) {
+        const bool tile_check = TILE_CHECK && !viewer && helper < 0;
+        if (tile_check && R.blk_base >= 0) {
             bool full = false;
             if (tid < 5) {
                 const int px = tx + (tid == 1) - (tid == 2), py = ty + (tid == 3) - (tid == 4);
@@ -1451,7 +1466,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // take the nearest candidates, one each, against all 16 segments.
         bool tile_blocked = pre_blocked;
         corner_tests += pre_tests;
-        if (TILE_CHECK && !viewer && helper < 0 && !pre_blocked) {
+        if (tile_check && !pre_blocked) {
             bool full = false;
             if (tid < min(n_smem, kThreads)) {
                 full = box_blocks_tile(R, s_box[2 * tid], s_box[2 * tid + 1], R.x_coord[ix0], R.x_coord[ix1 - 1],
@@ -1640,18 +1655,18 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                 }
                 // the pyramid filter pays for its set-up only on long candidate lists
                 Plane *pyr = s_pyr[warp];
-                const int npyr = count > kPyramidMinCount ? pyramid_planes(R, qu, qn, qw, pyr) : 0;
+                const bool use_pyr = count > kPyramidMinCount;
                 float v;
                 if (EXTRA && (R.cone || (R.flags & VCM_TWO_SIDED))) {
                     // sides and cone: one sweep variant of their own (8 rows
                     // per pass; the host sets k_rows = 8 for these requests)
                     v = sweep_viewpoint<8, true>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr,
-                                                 npyr, tests, rechecks, sc.n_boxes);
+                                                 use_pyr, tests, rechecks, sc.n_boxes);
                 } else switch (R.k_rows) {
-                case 1: v = sweep_viewpoint<1, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
-                case 2: v = sweep_viewpoint<2, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
-                case 4: v = sweep_viewpoint<4, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
-                default: v = sweep_viewpoint<8, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, npyr, tests, rechecks, sc.n_boxes); break;
+                case 1: v = sweep_viewpoint<1, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, use_pyr, tests, rechecks, sc.n_boxes); break;
+                case 2: v = sweep_viewpoint<2, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, use_pyr, tests, rechecks, sc.n_boxes); break;
+                case 4: v = sweep_viewpoint<4, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, use_pyr, tests, rechecks, sc.n_boxes); break;
+                default: v = sweep_viewpoint<8, false>(R, s_box, n_smem, list_tail, count, gbox, qu, qn, qw, front, vp, pyr, use_pyr, tests, rechecks, sc.n_boxes); break;
                 }
                 if (!front)
                     v = 0.f;
