@@ -741,7 +741,7 @@ def sub_serve(ctx, args, sampler):
                 ctx.vcm_poll(t, -1)
                 _, hc, _, stt = ctx.vcm_result_get(t, copy=False)
                 lat2[i] = (ts - arr[i]) * 1e3 + stt["latency_ms"]
-                info[i] = {k: stt[k] for k in ("queue_ms", "device_ms", "group_size", "launch_form")}
+                info[i] = {k: stt[k] for k in ("queue_ms", "device_ms", "launch_ms", "group_size", "launch_form")}
                 ctx.vcm_result_release(t)
 
         for t in [ctx.vcm_submit(r) for r in picks[:4]]:

@@ -204,6 +204,7 @@ typedef struct {
                                   wait for the kernels of the launch before it */
     uint32_t group_size;       /* requests in that launch */
     uint32_t launch_form;      /* VCM_FORM_* of that launch */
+    double launch_ms;          /* host time the scheduler spent enqueuing that launch */
 } vcm_result;
 
 /* How the scheduler launched a group (vcm_result.launch_form).

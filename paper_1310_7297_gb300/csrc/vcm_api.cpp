@@ -574,6 +574,7 @@ struct Ticket {
     Slot *slot = nullptr;
     std::chrono::steady_clock::time_point t_submit, t_launch, t_done;
     double device_ms = 0.0;
+    double launch_ms = 0.0;   // host time to enqueue its launch
     uint32_t group_size = 0, form = 0;
     std::shared_ptr<CacheEntry> cache_fill;   // cached bits this request's launch writes
     std::shared_ptr<CacheEntry> cache_hit;    // cached bits it is recoloured from
@@ -1322,9 +1323,12 @@ void launch_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Ticket>> &g
             cudaMemcpyAsync(t.h_stats, s.d_stats + i, sizeof(vcm_stats), cudaMemcpyDeviceToHost, s.stream);
         }
         if (cudaEventRecord(s.t1, s.stream) == cudaSuccess && cudaEventRecord(s.done, s.stream) == cudaSuccess) {
+            const double host_ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - now).count();
             for (auto &t : group) {
                 t->state = T_RUNNING;
                 t->slot = &s;
+                t->launch_ms = host_ms;
             }
             s.inflight = group;
             ctx->last_launched = &s;
@@ -1405,6 +1409,7 @@ void launch_recolor_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Tic
     if (st == VCM_OK)
         st = body();
     if (st == VCM_OK) {
+        t.launch_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t.t_launch).count();
         t.state = T_RUNNING;
         t.slot = &s;
         s.inflight = group;
@@ -2140,6 +2145,7 @@ vcm_status vcm_result_get(vcm_ctx *ctx, uint64_t ticket, vcm_result *out)
     out->device_ms = t.device_ms;
     out->group_size = t.group_size;
     out->launch_form = t.form;
+    out->launch_ms = t.launch_ms;
     return VCM_OK;
 }
 
