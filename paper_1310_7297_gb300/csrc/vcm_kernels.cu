@@ -739,17 +739,19 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
             g = 0.f;
         };
         for (int rp = 0; rp < R.row_passes && !(strict_exit && strict_fail); ++rp) {
-            float inv_w[K], clampv[K];
+            // per row: its w offset dw and the band of its test in w units,
+            // tau |dw|; -inf once the row is blocked (or past the patch grid)
+            float dwv[K], thr[K];
             unsigned valid = 0, sgnw = 0;
 #pragma unroll
             for (int m = 0; m < K; ++m) {
                 const int iw = (rp * K + m) * G + g;
                 const bool ok = col_ok && iw < R.nw;
                 const float dw = w_coord[ok ? iw : 0] - qw;
-                inv_w[m] = rcp_approx(dw);
+                dwv[m] = dw;
                 if (dw >= 0.f)
                     sgnw |= 1u << m;
-                clampv[m] = ok ? 0.f : f_inf();
+                thr[m] = ok ? kBand * fabsf(dw) : -f_inf();
                 if (ok)
                     valid |= 1u << m;
             }
@@ -803,24 +805,40 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                 if (__all_sync(kFull, alive == 0 || (pre_x - pre_e) < -kBand))
                     continue;
                 ++nb;   // boxes whose rows are tested
-                const float a_w = lo.z - qw, b_w = hi.z - qw;
+                // The column's segment is inside the box's u and n slabs for
+                // t in [pre_e, pre_x]; a row meets the box when the w offsets
+                // the segment takes there, t * dw, reach the box's w extent
+                // [a_w, b_w]: e1 = a_w - (the larger end) < 0 and e2 = (the
+                // smaller end) - b_w < 0.  Both are t-margins times |dw|, so the
+                // band is tau |dw|, and the column's own margin pre_x - pre_e
+                // joins them (a hit needs it above tau; below -tau no row
+                // meets the box).  The w extent of a 2D request is unbounded.
+                const float lm = pre_x - pre_e;
+                const bool lane_sure = lm > kBand;
+                float a_w = lo.z - qw, b_w = hi.z - qw;
+                if (R.dims != 3) {
+                    a_w = -f_inf();
+                    b_w = f_inf();
+                }
+                if (lm < -kBand) {   // e1 and e2 are +inf or NaN: no row enters
+                    a_w = f_inf();
+                    b_w = -f_inf();
+                }
 #pragma unroll
                 for (int m = 0; m < K; ++m) {
                     const bool sp = (sgnw >> m) & 1u;
-                    const float tnw = (sp ? a_w : b_w) * inv_w[m];
-                    const float tfw = (sp ? b_w : a_w) * inv_w[m];
-                    const float enter = fmaxf(fmaxf(pre_e, tnw), clampv[m]);
-                    const float exit_ = fminf(pre_x, tfw);
-                    const float mv = exit_ - enter;
-                    if (mv >= -kBand) {
-                        bool hit = mv > kBand;
+                    const float e1 = fmaf(-(sp ? pre_x : pre_e), dwv[m], a_w);
+                    const float e2 = fmaf(sp ? pre_e : pre_x, dwv[m], -b_w);
+                    const float mm = fmaxf(e1, e2);
+                    if (mm <= thr[m] && ((alive >> m) & 1u)) {
+                        bool hit = lane_sure && mm < -thr[m];
                         if (!hit) {
                             const int iw = (rp * K + m) * G + g;
                             hit = exact_hit(qu, qn, qw, pu, R.p_n, w_coord[iw], lo, hi);
                             ++rechecks;
                         }
                         if (hit) {
-                            clampv[m] = f_inf();
+                            thr[m] = -f_inf();
                             alive &= ~(1u << m);
                         }
                     }
@@ -957,7 +975,11 @@ __device__ __forceinline__ void add_candidate(const float4 *__restrict__ world, 
 // decides whole tiles, which pays when a viewpoint's own work is large (the
 // 100,000-box scene with 64 x 32 patches: -10 %); in the other instantiation
 // its code alone cost a few % on smaller requests.
-template <bool EXTRA, bool TILE_CHECK>
+//
+// CHUNKS: the second pass's instantiation, which takes the published chunks
+// and holds none of the tile pass's code (the cull, the sort, the checks and
+// the publication), so its registers and instructions fit the sweep alone.
+template <bool EXTRA, bool TILE_CHECK, bool CHUNKS>
 __global__ void __launch_bounds__(kThreads, 5)
 k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict__ tile_prefix,
         int n_req, int total_tiles, int *__restrict__ work, int *__restrict__ spill_all, int box_cap,
@@ -1016,18 +1038,18 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // hull points (one barrier for all of it).  With one_tile, block b
         // does tile b only and exits, so blocks of concurrent launches
         // interleave (a persistent grid would hold every SM to the end).
-        // The second pass (share == 2) takes the chunks the first published,
+        // The second pass (CHUNKS, share == 2) takes the chunks the first published,
         // in order, and no tiles.
         if (tid == 0) {
             int took = -1, it;
-            if (share == 2) {
+            if (CHUNKS) {
                 const int h = atomicAdd(work + 3, 1);
                 took = h < min(__ldcg(work + 2), kChunkCap) ? h : -1;
             }
             if (took >= 0) {
                 const int rec = __ldcg(work + kWorkHeader + kChunkOff + (size_t)(2 + kChunkVp) * took);
                 it = __ldcg(work + kWorkHeader + kRecOff + (size_t)kRecInts * rec);
-            } else if (share == 2) {
+            } else if (CHUNKS) {
                 it = total_tiles;
             } else {
                 it = one_tile ? (sm.item == -2 ? total_tiles : (int)blockIdx.x) : atomicAdd(work, 1);
@@ -1130,7 +1152,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         const bool viewer = (R.flags & VCM_VIEWER) != 0;
         const bool any_front = viewer || (R.flags & VCM_TWO_SIDED) ||
                                (R.sn > 0.f ? (qn_hi - R.p_n > 0.f) : (R.p_n - qn_lo > 0.f));
-        if (!any_front && !want_bits) {
+        if (!CHUNKS && !any_front && !want_bits) {
             for (int i = tid; i < tn; i += kThreads) {
                 const int ix = ix0 + i % tw, iy = iy0 + i / tw;
                 put_v(R, ((long long)layer * R.ny + iy) * R.nx + ix, 0.f);
@@ -1153,7 +1175,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         const int tile_pos = ty * R.tiles_x + tx;
         bool pre_blocked = false;
         unsigned long long pre_tests = 0;
-        const bool tile_check = TILE_CHECK && !viewer && helper < 0;
+        const bool tile_check = TILE_CHECK && !CHUNKS && !viewer;
         if (tile_check && R.blk_base >= 0) {
             bool full = false;
             if (tid < 5) {
@@ -1177,7 +1199,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // candidates past the staged ones: the block's spill region for its
         // own tile, the record's ids in the pool for a chunk
         const int *list_tail = spill;
-        if (helper < 0 && !pre_blocked) {
+        if (!CHUNKS && !pre_blocked) {
             hull_planes(R.dims, s_pts, np, sm);
             __syncthreads();
         }
@@ -1193,7 +1215,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // is spanned by the interval's two ends.  Rows are taken 128 at a
         // time: one thread finds a row's span, a block scan lays the spans
         // end to end, and the threads share out the cells.
-        if (helper < 0 && !pre_blocked) {
+        if (!CHUNKS && !pre_blocked) {
             float ax0 = s_pts[0][0], ax1 = ax0, ay0 = s_pts[0][1], ay1 = ay0;
             for (int l = 1; l < 4; ++l) {
                 ax0 = fminf(ax0, s_pts[l][0]); ax1 = fmaxf(ax1, s_pts[l][0]);
@@ -1340,7 +1362,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
                     s_npass = 0;
                 __syncthreads();   // the next rows reuse the span arrays
             }
-        } else if (helper >= 0) {
+        } else if (CHUNKS) {
             // a chunk: the owner's candidate list, in the owner's order, and
             // the chunk's viewpoints
             const int *ch = work + kWorkHeader + kChunkOff + (size_t)(2 + kChunkVp) * helper;
@@ -1369,7 +1391,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // most sightlines, so the all-blocked exits come early.  Keys are the
         // squared footprint distance from the tile centre (a positive float,
         // so its bits order like the value) above the sorted box index.
-        if (helper < 0 && n_smem > 1) {
+        if (!CHUNKS && n_smem > 1) {
             const float cx = 0.5f * (R.x_coord[ix0] + R.x_coord[ix1 - 1]);
             const float cy = 0.5f * (R.y_coord[iy0] + R.y_coord[iy1 - 1]);
             auto key_of = [&](int i) {
@@ -1491,7 +1513,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             if (tid == 0)
                 shortcuts += (unsigned)tn;
         }
-        if (viewer) {
+        if (!CHUNKS && viewer) {
             // viewer-centric: threads take cells, one segment each
             for (int vi = tid; vi < tn; vi += kThreads) {
                 const int ry = (int)(((float)vi + 0.5f) * inv_tw), ix = ix0 + vi - ry * tw, iy = iy0 + ry;
@@ -1510,7 +1532,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // is almost always among them); the viewpoints it leaves open are
         // listed and then taken one per warp for the check over the 32
         // nearest and the separable sweep.
-        for (; !viewer && !tile_blocked && helper < 0;) {
+        for (; !CHUNKS && !viewer && !tile_blocked;) {
             int base = 0;
             if (lane == 0)
                 base = atomicAdd(&s_next, 4);
@@ -1572,7 +1594,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         // again; a spilled list's tail is read from the record), and a tile
         // whose publication would pass a cap of the arena keeps its
         // viewpoints.
-        if (share == 1 && spill_slot >= 0 && n_und >= R.min_publish &&
+        if (!CHUNKS && share == 1 && spill_slot >= 0 && n_und >= R.min_publish &&
             (count <= kPublishBoxes || n_und >= kPublishHeavy)) {
             int *arena = work + kWorkHeader;
             const int cvp = R.chunk_vp;
@@ -1696,7 +1718,7 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
         if (lane == 0 && rechecks)
             atomicAdd(&R.stats->rechecked, (unsigned long long)rechecks);
         if (tid == 0) {
-            if (sm.helper < 0)
+            if (!CHUNKS)
                 atomicAdd(&R.stats->boxes_listed, (unsigned long long)count);
             sm.item = -2;   // one_tile: the next round exits
         }
@@ -1934,8 +1956,9 @@ cudaError_t init_device()
             }
     if ((e = cudaMemcpyToSymbol(c_tri, tri, sizeof(tri))) != cudaSuccess)
         return e;
-    const void *kernels[4] = {(const void *)k_tiles<false, false>, (const void *)k_tiles<true, false>,
-                              (const void *)k_tiles<false, true>, (const void *)k_tiles<true, true>};
+    const void *kernels[6] = {(const void *)k_tiles<false, false, false>, (const void *)k_tiles<true, false, false>,
+                              (const void *)k_tiles<false, true, false>,  (const void *)k_tiles<true, true, false>,
+                              (const void *)k_tiles<false, false, true>,  (const void *)k_tiles<true, false, true>};
     for (const void *k : kernels)
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)tiles_smem_bytes(kMaxBoxCap))) != cudaSuccess)
@@ -2018,7 +2041,8 @@ int tiles_blocks_per_sm(int box_cap)
 {
     // all instantiations have the same launch bounds (5 blocks of kThreads)
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tiles<false, false>, kThreads, tiles_smem_bytes(box_cap)) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tiles<false, false, false>, kThreads,
+                                                      tiles_smem_bytes(box_cap)) !=
         cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
@@ -2042,8 +2066,9 @@ cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int
             return cudaErrorInvalidValue;
         grid_blocks = total_tiles;
     }
-    auto kernel = extra ? (tile_check ? k_tiles<true, true> : k_tiles<true, false>)
-                        : (tile_check ? k_tiles<false, true> : k_tiles<false, false>);
+    auto kernel = extra ? (tile_check ? k_tiles<true, true, false> : k_tiles<true, false, false>)
+                        : (tile_check ? k_tiles<false, true, false> : k_tiles<false, false, false>);
+    auto chunks = extra ? k_tiles<true, false, true> : k_tiles<false, false, true>;
     share = share && !one_tile;
     kernel<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles, d_work, d_spill,
                                                     box_cap, one_tile ? 1 : 0, d_spill_busy, slots, share ? 1 : 0,
@@ -2053,7 +2078,7 @@ cudaError_t launch_tiles(const DevScene &sc, const DevRequest *d_reqs, const int
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess)
             return e;
-        kernel<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles, d_work,
+        chunks<<<grid_blocks, kThreads, smem, stream>>>(sc, d_reqs, d_tile_prefix, n_req, total_tiles, d_work,
                                                         d_spill, box_cap, 0, d_spill_busy, slots, 2, claim_rounds);
     }
     return cudaGetLastError();
