@@ -726,9 +726,9 @@ def sub_serve(ctx, args, sampler):
                 "segments_per_s": seg / max(done), "clocks": sampler.window(t_w, time.monotonic(), "FIFO arm"),
                 "median_wait_ms": float(np.median([1e3 * (began[i] - arr[i]) for i in range(n)])),
                 "median_service_ms": float(np.median([1e3 * (done[i] - began[i]) for i in range(n)])),
-                "slowest": [{"latency_ms": lat[i], "wait_ms": 1e3 * (began[i] - arr[i]),
-                             "service_ms": 1e3 * (done[i] - began[i]), "segments": seg_of[i % len(pool)]}
-                            for i in slow]}
+                "slowest": [{"request": int(i), "arrival_ms": 1e3 * arr[i], "latency_ms": lat[i],
+                             "wait_ms": 1e3 * (began[i] - arr[i]), "service_ms": 1e3 * (done[i] - began[i]),
+                             "segments": seg_of[i % len(pool)]} for i in slow]}
 
         # continuous batching through the scheduler; a consumer thread takes
         # each result as it is done and releases it, as a server would
@@ -741,7 +741,8 @@ def sub_serve(ctx, args, sampler):
                 ctx.vcm_poll(t, -1)
                 _, hc, _, stt = ctx.vcm_result_get(t, copy=False)
                 lat2[i] = (ts - arr[i]) * 1e3 + stt["latency_ms"]
-                info[i] = {k: stt[k] for k in ("queue_ms", "device_ms", "launch_ms", "group_size", "launch_form")}
+                info[i] = {k: stt[k] for k in ("queue_ms", "device_ms", "chain_ms", "launch_ms", "group_size",
+                                               "launch_form")}
                 ctx.vcm_result_release(t)
 
         for t in [ctx.vcm_submit(r) for r in picks[:4]]:
@@ -767,9 +768,13 @@ def sub_serve(ctx, args, sampler):
                 "mean_group_size": float(np.mean([x["group_size"] for x in info])),
                 "median_queue_ms": float(np.median([x["queue_ms"] for x in info])),
                 "median_device_ms": float(np.median([x["device_ms"] for x in info])),
+                "median_chain_ms": float(np.median([x["chain_ms"] for x in info])),
                 "median_host_ms": float(np.median([lat2[i] - info[i]["queue_ms"] - info[i]["device_ms"]
                                                    for i in range(n)])),
-                "slowest": [dict(latency_ms=lat2[i], segments=seg_of[i % len(pool)], **info[i]) for i in slow]}
+                "slowest": [dict(request=int(i), arrival_ms=1e3 * arr[i], latency_ms=lat2[i], fifo_latency_ms=lat[i],
+                                 segments=seg_of[i % len(pool)], **info[i]) for i in slow]}
+        for x in fifo["slowest"]:   # the same requests in the other arm
+            x["continuous_latency_ms"] = lat2[x["request"]]
         out.append({"rate_per_s": rate, "requests": n, "continuous": cont, "one_per_launch_fifo": fifo})
     ctx.vcm_set_slots(2, 64)
     return {"workload": "Poisson arrivals of requests from the batched mix against a resident 100,000-box scene",

@@ -205,6 +205,8 @@ typedef struct {
     uint32_t group_size;       /* requests in that launch */
     uint32_t launch_form;      /* VCM_FORM_* of that launch */
     double launch_ms;          /* host time the scheduler spent enqueuing that launch */
+    double chain_ms;           /* of device_ms, the wait for the kernels of the launch before it
+                                  (0 when that launch had finished) */
 } vcm_result;
 
 /* How the scheduler launched a group (vcm_result.launch_form).

@@ -454,6 +454,8 @@ struct Slot {
     cudaEvent_t done = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr;   // device time of the in-flight launch
     cudaEvent_t kernels_done = nullptr;       // its last kernel (before the result copies)
+    cudaEvent_t t_chain = nullptr;            // where its wait for the launch before it ended
+    bool chained = false;                     // t_chain recorded for the in-flight launch
     std::vector<std::shared_ptr<::Ticket>> inflight;
     bool posted = false;
     std::thread waiter;
@@ -575,6 +577,7 @@ struct Ticket {
     std::chrono::steady_clock::time_point t_submit, t_launch, t_done;
     double device_ms = 0.0;
     double launch_ms = 0.0;   // host time to enqueue its launch
+    double chain_ms = 0.0;    // device wait for the launch before it
     uint32_t group_size = 0, form = 0;
     std::shared_ptr<CacheEntry> cache_fill;   // cached bits this request's launch writes
     std::shared_ptr<CacheEntry> cache_hit;    // cached bits it is recoloured from
@@ -927,8 +930,13 @@ vcm_status record_launch(vcm_ctx *ctx, Slot &s, const Prepared &P, vcm_stats *st
         CUDA_TRY(cudaMemsetAsync(s.d_work + kWorkHeader + kBlockerOff, 0xFF, (size_t)P.L.blocker_ints * sizeof(int),
                                  stream));
     // the tile kernel starts after another launch's kernels (see launch_group)
-    if (after)
+    if (after) {
         CUDA_TRY(cudaStreamWaitEvent(stream, after, 0));
+        if (!capturing && s.t_chain) {
+            CUDA_TRY(cudaEventRecord(s.t_chain, stream));
+            s.chained = true;
+        }
+    }
     // fault injection: every spill region already held (any nonzero word)
     if (hold_spill)
         CUDA_TRY(cudaMemsetAsync(s.d_spill_busy, 1, s.spill_busy_cap * sizeof(int), stream));
@@ -985,6 +993,7 @@ vcm_status enqueue_graph(vcm_ctx *ctx, Slot &s, const std::vector<const Canon *>
         (unsigned long long)P.tile_check, ptr(s.d_desc), ptr(s.h_desc), ptr(s.d_work), ptr(s.d_spill),
         ptr(s.d_spill_busy), ptr(stats)};
     direct_only = direct_only || after != nullptr;   // a graph holds no wait on another stream's event
+    s.chained = false;
     if (!direct_only && s.exec[f] && s.key[f] == key) {
         CUDA_TRY(cudaGraphLaunch(s.exec[f], s.stream));
         CUDA_TRY(cudaEventRecord(s.desc_copied, s.stream));
@@ -1153,14 +1162,19 @@ void slot_waiter(vcm_ctx *ctx, Slot *s)
         lk.unlock();
         const cudaError_t e = cudaEventSynchronize(ev);
         const auto now = std::chrono::steady_clock::now();
-        float dev_ms = 0.f;
+        float dev_ms = 0.f, chain_ms = 0.f;
         if (e == cudaSuccess && cudaEventElapsedTime(&dev_ms, s->t0, s->t1) != cudaSuccess) {
             cudaGetLastError();
             dev_ms = 0.f;
         }
+        if (e == cudaSuccess && s->chained && cudaEventElapsedTime(&chain_ms, s->t0, s->t_chain) != cudaSuccess) {
+            cudaGetLastError();
+            chain_ms = 0.f;
+        }
         lk.lock();
         for (auto &t : group) {
             t->device_ms = dev_ms;
+            t->chain_ms = chain_ms;
             const uint32_t derr = t->h_stats ? t->h_stats->error : 0u;
             if (e != cudaSuccess) {
                 t->state = T_ERROR;
@@ -1384,8 +1398,12 @@ void launch_recolor_group(vcm_ctx *ctx, Slot &s, std::vector<std::shared_ptr<Tic
         CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, L.bytes, cudaMemcpyHostToDevice, s.stream));
         CUDA_TRY(cudaEventRecord(s.desc_copied, s.stream));
         CUDA_TRY(cudaMemsetAsync(s.d_stats, 0, sizeof(vcm_stats), s.stream));
-        if (after)
+        s.chained = false;
+        if (after) {
             CUDA_TRY(cudaStreamWaitEvent(s.stream, after, 0));
+            CUDA_TRY(cudaEventRecord(s.t_chain, s.stream));
+            s.chained = true;
+        }
         const DevRequest *d_reqs = reinterpret_cast<const DevRequest *>(s.d_desc + L.off_reqs);
         const long long *d_vps = reinterpret_cast<const long long *>(s.d_desc + L.off_vps);
         int *list = nullptr;   // the viewpoints that need a measure, and their count
@@ -1641,6 +1659,7 @@ vcm_status start_scheduler(vcm_ctx *ctx, uint32_t n_slots)
         CUDA_TRY(cudaEventCreate(&s->t0));
         CUDA_TRY(cudaEventCreate(&s->t1));
         CUDA_TRY(cudaEventCreateWithFlags(&s->kernels_done, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreate(&s->t_chain));
         s->scheduler = true;
         ctx->slots.push_back(std::move(s));
     }
@@ -1685,7 +1704,8 @@ void destroy_slot(Slot &s)
     if (s.t0) cudaEventDestroy(s.t0);
     if (s.t1) cudaEventDestroy(s.t1);
     if (s.kernels_done) cudaEventDestroy(s.kernels_done);
-    s.t0 = s.t1 = s.kernels_done = nullptr;
+    if (s.t_chain) cudaEventDestroy(s.t_chain);
+    s.t0 = s.t1 = s.kernels_done = s.t_chain = nullptr;
     if (s.stream) cudaStreamDestroy(s.stream);
     s.inflight.clear();
     s.stream = nullptr;
@@ -2146,6 +2166,7 @@ vcm_status vcm_result_get(vcm_ctx *ctx, uint64_t ticket, vcm_result *out)
     out->group_size = t.group_size;
     out->launch_form = t.form;
     out->launch_ms = t.launch_ms;
+    out->chain_ms = t.chain_ms;
     return VCM_OK;
 }
 

@@ -75,7 +75,8 @@ class vcm_result(ctypes.Structure):
                 ("d_color", ctypes.c_void_p), ("d_bits", ctypes.c_void_p), ("n_viewpoints", ctypes.c_uint64),
                 ("words_per_viewpoint", ctypes.c_uint32), ("stats", vcm_stats), ("latency_ms", ctypes.c_double),
                 ("queue_ms", ctypes.c_double), ("device_ms", ctypes.c_double), ("group_size", ctypes.c_uint32),
-                ("launch_form", ctypes.c_uint32), ("launch_ms", ctypes.c_double)]
+                ("launch_form", ctypes.c_uint32), ("launch_ms", ctypes.c_double),
+                ("chain_ms", ctypes.c_double)]
 
 
 class vcm_memory(ctypes.Structure):
@@ -344,7 +345,7 @@ class Context:
             v, c = v.copy(), c.copy()
             b = b.copy() if b is not None else None
         st = {k: getattr(res.stats, k) for k, _ in vcm_stats._fields_}
-        for k in ("latency_ms", "queue_ms", "device_ms", "group_size", "launch_form", "launch_ms"):
+        for k in ("latency_ms", "queue_ms", "device_ms", "group_size", "launch_form", "launch_ms", "chain_ms"):
             st[k] = getattr(res, k)
         return v, c, b, st
 
@@ -368,7 +369,7 @@ class Context:
         # bit words as int32 (the same 32 bits; torch's uint32 support is partial)
         b = view(res.d_bits, (n, res.words_per_viewpoint), "<i4") if res.d_bits else None
         st = {k: getattr(res.stats, k) for k, _ in vcm_stats._fields_}
-        for k in ("latency_ms", "queue_ms", "device_ms", "group_size", "launch_form", "launch_ms"):
+        for k in ("latency_ms", "queue_ms", "device_ms", "group_size", "launch_form", "launch_ms", "chain_ms"):
             st[k] = getattr(res, k)
         return v, c, b, st
 
