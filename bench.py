@@ -673,6 +673,17 @@ def sub_serve(ctx, args, sampler):
             h_c[:n].copy_(d_c[:n], non_blocking=True)
         stream.synchronize()
 
+    def sched_one(r):
+        t = ctx.vcm_submit(r)
+        ctx.vcm_poll(t, -1)
+        ctx.vcm_result_release(t)
+
+    def busy(run_one, seconds=0.5):
+        t_end, k = time.monotonic() + seconds, 0
+        while time.monotonic() < t_end:
+            run_one(pool[k % len(pool)])
+            k += 1
+
     for r in pool:
         fifo_one(r)
     # warm the scheduler path too: every request once, alone and in a burst
@@ -690,13 +701,14 @@ def sub_serve(ctx, args, sampler):
         arr = synth.poisson_arrivals(int(rate), float(rate), n)
         picks = [pool[i % len(pool)] for i in range(n)]
         seg = sum(seg_of[i % len(pool)] for i in range(n))
-        # no garbage collection during the arms, and a few untimed requests
-        # through each arm first (a stalled harness thread is not a latency
-        # of either path)
+        # No garbage collection during the arms (a stalled harness thread is
+        # not a latency of either path), and each arm starts on a busy GPU:
+        # 0.5 s of back-to-back requests through its own path first.  After
+        # half a second idle the next large request ran up to twice as long
+        # (3.9-6.6 ms against 3.34), in either arm.
         gc.collect()
         gc.disable()
-        for r in picks[:4]:
-            fifo_one(r)
+        busy(fifo_one)
 
         # FIFO server, one request per launch
         q = _queue.Queue()
@@ -720,10 +732,11 @@ def sub_serve(ctx, args, sampler):
                 time.sleep(arr[i] - now)
             q.put((i, t0))
         th.join()
+        t_fifo = (t_w, time.monotonic())
         lat = [1e3 * (done[i] - arr[i]) for i in range(n)]
         slow = np.argsort(lat)[-3:][::-1]
         fifo = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "segments_per_s": seg / max(done), "clocks": sampler.window(t_w, time.monotonic(), "FIFO arm"),
+                "segments_per_s": seg / max(done),
                 "median_wait_ms": float(np.median([1e3 * (began[i] - arr[i]) for i in range(n)])),
                 "median_service_ms": float(np.median([1e3 * (done[i] - began[i]) for i in range(n)])),
                 "slowest": [{"request": int(i), "arrival_ms": 1e3 * arr[i], "latency_ms": lat[i],
@@ -745,9 +758,7 @@ def sub_serve(ctx, args, sampler):
                                                "launch_form")}
                 ctx.vcm_result_release(t)
 
-        for t in [ctx.vcm_submit(r) for r in picks[:4]]:
-            ctx.vcm_poll(t, -1)
-            ctx.vcm_result_release(t)
+        busy(sched_one)
         th2 = threading.Thread(target=consumer)
         th2.start()
         t_w = time.monotonic()
@@ -759,11 +770,15 @@ def sub_serve(ctx, args, sampler):
             ts = time.perf_counter() - t0   # the library times from here to completion
             q2.put((i, ctx.vcm_submit(picks[i]), ts))
         th2.join()
+        t_cont = (t_w, time.monotonic())
         gc.enable()
+        # clock windows once both arms are done (their wait for the last
+        # sample would otherwise idle the GPU before the second arm)
+        fifo["clocks"] = sampler.window(*t_fifo, "FIFO arm")
         last = max(arr[i] + lat2[i] / 1e3 for i in range(n))
         slow = np.argsort(lat2)[-3:][::-1]
         cont = {"p50_ms": float(np.percentile(lat2, 50)), "p99_ms": float(np.percentile(lat2, 99)),
-                "segments_per_s": seg / last, "clocks": sampler.window(t_w, time.monotonic(), "continuous arm"),
+                "segments_per_s": seg / last, "clocks": sampler.window(*t_cont, "continuous arm"),
                 "persistent_launch_share": float(np.mean([x["launch_form"] == 0 for x in info])),
                 "mean_group_size": float(np.mean([x["group_size"] for x in info])),
                 "median_queue_ms": float(np.median([x["queue_ms"] for x in info])),
@@ -1090,7 +1105,7 @@ def main():
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--serve-count", type=int, default=400)
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--rates", type=float, nargs="+", default=[50, 100, 200, 500, 1000, 2000])
     ap.add_argument("--slots", type=int, default=2)
     ap.add_argument("--max-batch", type=int, default=8)
