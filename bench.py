@@ -50,11 +50,12 @@ GRID_CELL_LARGE_M = 50.0
 # min of exits, then one compare: 6 FMUL + 12 FMNMX + 1 compare = 19 FP32
 # operations in 3D, 13 in 2D.  Every test the tile kernel counts (row tests
 # of the sweep, corner tests of the one-box checks) decides one
-# segment/box pair.  The separable sweep itself issues only ~7 lane
-# operations per row test, sharing the u and n parts across a column's rows;
-# those are reported beside the fraction.
+# segment/box pair.  The separable sweep itself issues only ~6 lane
+# operations per row test (two selects, two fused w-margins, their max and a
+# compare), sharing the u and n parts across a column's rows; those are
+# reported beside the fraction.
 OPS_PER_SLAB_TEST = {3: 19, 2: 13}
-ISSUED_OPS_PER_ROW_TEST = 7
+ISSUED_OPS_PER_ROW_TEST = 6
 ISSUED_OPS_PER_CORNER_TEST = 15
 L2_FLUSH_BYTES = 512 << 20
 # kernels of ours that one step launches: k_prologue, k_tiles (two passes:
