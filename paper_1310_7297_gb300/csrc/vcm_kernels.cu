@@ -859,16 +859,18 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
                     if (!((valid >> m) & 1u))
                         continue;
                     const bool blocked = !((alive >> m) & 1u);
-                    const int iw = (rp * K + m) * G + g;
                     if (blocked) {
                         if (want_bits) {
+                            const int iw = (rp * K + m) * G + g;
                             const int j = iw * R.nu + iu;
                             if (IN_BOUNDS(vp * R.words + (j >> 5), (long long)R.nx * R.ny * R.nl * R.words, R.stats))
                                 atomicOr(&R.bits_out[vp * R.words + (j >> 5)], 1u << (j & 31));
                         }
                     } else if (front) {
-                        // |r|^2 = (ru^2 + rn^2) of the column + rw^2 of the row
-                        const float rw = qw - w_coord[iw];
+                        // |r|^2 = (ru^2 + rn^2) of the column + rw^2 of the row;
+                        // rw = q_w - w is the row's offset negated (round to
+                        // nearest is symmetric, so exactly -dw)
+                        const float rw = -dwv[m];
                         if (EXTRA && R.cone && !in_cone(R, ru, rn, rw))
                             continue;   // q is outside this patch's field of view
                         const float d2 = fmaf(rw, rw, col_d2);
