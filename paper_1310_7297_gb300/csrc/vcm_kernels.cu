@@ -706,6 +706,7 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
     const float inv_n = rcp_approx(dn);
     const bool sgn_n = dn >= 0.f;
     const bool want_bits = (R.flags & VCM_EMIT_BITS) && R.bits_out;
+    const bool is3d = R.dims == 3;
     // strict: any blocked patch zeroes the viewpoint, so the first one ends it
     const bool strict = (R.flags & VCM_STRICT) != 0;
     const bool strict_exit = strict && !want_bits;
@@ -852,40 +853,42 @@ __device__ __forceinline__ float sweep_viewpoint(const DevRequest &R, const floa
             tests += (unsigned long long)nb * K;
             if (strict)
                 strict_fail |= __any_sync(kFull, alive != valid);
-            // visible measure of the unblocked rows, and the blocked bits
-            if (want_bits || (!strict_fail && __any_sync(kFull, alive != 0))) {
+            // the blocked bits, and the visible measure of the unblocked rows
+            if (want_bits) {
 #pragma unroll
                 for (int m = 0; m < K; ++m) {
-                    if (!((valid >> m) & 1u))
-                        continue;
-                    const bool blocked = !((alive >> m) & 1u);
-                    if (blocked) {
-                        if (want_bits) {
-                            const int iw = (rp * K + m) * G + g;
-                            const int j = iw * R.nu + iu;
-                            if (IN_BOUNDS(vp * R.words + (j >> 5), (long long)R.nx * R.ny * R.nl * R.words, R.stats))
-                                atomicOr(&R.bits_out[vp * R.words + (j >> 5)], 1u << (j & 31));
-                        }
-                    } else if (front) {
-                        // |r|^2 = (ru^2 + rn^2) of the column + rw^2 of the row;
-                        // rw = q_w - w is the row's offset negated (round to
-                        // nearest is symmetric, so exactly -dw)
-                        const float rw = -dwv[m];
-                        if (EXTRA && R.cone && !in_cone(R, ru, rn, rw))
-                            continue;   // q is outside this patch's field of view
-                        const float d2 = fmaf(rw, rw, col_d2);
-                        float term;
-                        if (R.dims == 3) {
-                            const float ir = rsqrtf(d2);
-                            term = m_s * (ir * ir * ir);   // A |r| cos(theta) / |r|^3
-                        } else {
-                            term = m_s / d2;               // len |r| cos(theta) / |r|^2
-                        }
-                        // an add the compiler cannot fuse with the term's
-                        // product, so every specialised copy of this loop
-                        // rounds the same way
-                        psum = __fadd_rn(psum, term);
+                    if (((valid & ~alive) >> m) & 1u) {
+                        const int iw = (rp * K + m) * G + g;
+                        const int j = iw * R.nu + iu;
+                        if (IN_BOUNDS(vp * R.words + (j >> 5), (long long)R.nx * R.ny * R.nl * R.words, R.stats))
+                            atomicOr(&R.bits_out[vp * R.words + (j >> 5)], 1u << (j & 31));
                     }
+                }
+            }
+            const unsigned open = front && !strict_fail ? (valid & alive) : 0u;
+            if (__any_sync(kFull, open != 0u)) {
+#pragma unroll
+                for (int m = 0; m < K; ++m) {
+                    if (!((open >> m) & 1u))
+                        continue;
+                    // |r|^2 = (ru^2 + rn^2) of the column + rw^2 of the row;
+                    // rw = q_w - w is the row's offset negated (round to
+                    // nearest is symmetric, so exactly -dw)
+                    const float rw = -dwv[m];
+                    if (EXTRA && R.cone && !in_cone(R, ru, rn, rw))
+                        continue;   // q is outside this patch's field of view
+                    const float d2 = fmaf(rw, rw, col_d2);
+                    float term;
+                    if (is3d) {
+                        const float ir = rsqrtf(d2);
+                        term = m_s * (ir * ir * ir);   // A |r| cos(theta) / |r|^3
+                    } else {
+                        term = m_s / d2;               // len |r| cos(theta) / |r|^2
+                    }
+                    // an add the compiler cannot fuse with the term's
+                    // product, so every specialised copy of this loop
+                    // rounds the same way
+                    psum = __fadd_rn(psum, term);
                 }
             }
             // a group closes after every 8 of the lane's rows (K divides 8, so
