@@ -984,11 +984,16 @@ __device__ __forceinline__ void add_candidate(const float4 *__restrict__ world, 
 // CHUNKS: the second pass's instantiation, which takes the published chunks
 // and holds none of the tile pass's code (the cull, the sort, the checks and
 // the publication), so its registers and instructions fit the sweep alone.
-// It runs 6 blocks per SM (80 registers): the extra warps hide more latency
-// than its few spilled registers cost (100,000-box step 4.23 -> 4.03 ms,
-// 5,000-box step 0.354 -> 0.341 ms).
+//
+// Occupancy: the tile pass runs 6 blocks per SM (80 registers) and the chunk
+// pass 7 (72 registers).  Both spill some registers at these bounds, and
+// still the extra warps hide more latency than the spills cost.  Against 5
+// blocks for both (96 registers, no spills in the common instantiations):
+// 100,000-box step 4.23 -> 3.86 ms, 5,000-box step 0.354 -> 0.333 ms,
+// 256-request batch 91.5 -> 87.9 ms; 7 blocks for the tile pass too made
+// the batch 15 % slower.
 template <bool EXTRA, bool TILE_CHECK, bool CHUNKS>
-__global__ void __launch_bounds__(kThreads, CHUNKS ? 6 : 5)
+__global__ void __launch_bounds__(kThreads, CHUNKS ? 7 : 6)
 k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict__ tile_prefix,
         int n_req, int total_tiles, int *__restrict__ work, int *__restrict__ spill_all, int box_cap,
         int one_tile, int *__restrict__ spill_busy, int spill_slots, int share, int claim_rounds)
@@ -2048,7 +2053,7 @@ cudaError_t launch_grid_build(const float *d_lo_world, const float *d_hi_world, 
     return cudaGetLastError();
 }
 
-// Blocks of the chunk pass that fit on one SM (its launch bounds allow 6).
+// Blocks of the chunk pass that fit on one SM (its launch bounds allow 7).
 static int chunk_blocks_per_sm(int box_cap, bool extra)
 {
     int n = 0;
@@ -2060,7 +2065,7 @@ static int chunk_blocks_per_sm(int box_cap, bool extra)
 
 int tiles_blocks_per_sm(int box_cap)
 {
-    // the tile pass's instantiations share their launch bounds (5 blocks of kThreads)
+    // the tile pass's instantiations share their launch bounds (6 blocks of kThreads)
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tiles<false, false, false>, kThreads,
                                                       tiles_smem_bytes(box_cap)) !=
