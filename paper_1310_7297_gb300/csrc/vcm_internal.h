@@ -41,9 +41,11 @@ constexpr int kChunkVp = 16;
 constexpr int kMinPublish = 8;
 // Longer lists stay with their tile (the 100,000-box scene, lists of ~180
 // boxes on average: 6.44 ms with this limit, 6.71 ms without it) unless the
-// tile has at least kPublishHeavy open viewpoints.
+// tile has at least kPublishHeavy open viewpoints (32: 3.84 -> 3.82 ms
+// against 64; the tiles with 39-63 open viewpoints and lists just over 128
+// had set the end of the tile pass).
 constexpr int kPublishBoxes = 128;
-constexpr int kPublishHeavy = 64;
+constexpr int kPublishHeavy = 32;
 constexpr int kChunkCap = 262144;
 constexpr int kRecCap = 65536;
 constexpr int kRecInts = 3;
