@@ -1192,21 +1192,34 @@ k_tiles(DevScene sc, const DevRequest *__restrict__ reqs, const int *__restrict_
             int *blockers = work + kWorkHeader + kBlockerOff;
             const int tile_pos = ty * R.tiles_x + tx;
             bool full = false;
-            if (tid < 5) {
-                const int px = tx + (tid == 1) - (tid == 2), py = ty + (tid == 3) - (tid == 4);
-                const int cand = (px >= 0 && px < R.tiles_x && py >= 0 && py < R.tiles_y)
-                                     ? __ldcg(blockers + R.blk_base + py * R.tiles_x + px)
-                                     : -1;
-                if (cand >= 0 && cand < sc.n_boxes) {
-                    const float4 *gb = sc.boxes[R.perm];
-                    // the tile's corners from shared memory at each use, so that
-                    // they are not held in registers through the cull
-                    full = box_blocks_tile(R, __ldg(&gb[2 * cand]), __ldg(&gb[2 * cand + 1]), s_pts[0][0], s_pts[1][0],
-                                           s_pts[0][1], s_pts[2][1], zq);
-                    pre_tests = 16;
-                    if (full && tid != 0)
-                        blockers[R.blk_base + tile_pos] = cand;
+            if (warp == 0) {
+                // lanes 4c + k: candidate c (this position, then its four
+                // neighbours) against corner viewpoint k of the tile
+                const int c = lane >> 2, corner = lane & 3;
+                int cand = -1;
+                bool ok = false;
+                if (c < 5) {
+                    const int px = tx + (c == 1) - (c == 2), py = ty + (c == 3) - (c == 4);
+                    cand = (px >= 0 && px < R.tiles_x && py >= 0 && py < R.tiles_y)
+                               ? __ldcg(blockers + R.blk_base + py * R.tiles_x + px)
+                               : -1;
+                    if (cand >= 0 && cand < sc.n_boxes) {
+                        const float4 *gb = sc.boxes[R.perm];
+                        // the tile's corners from shared memory at each use, so that
+                        // they are not held in registers through the cull
+                        const float qx = (corner & 1) ? s_pts[1][0] : s_pts[0][0];
+                        const float qy = (corner & 2) ? s_pts[2][1] : s_pts[0][1];
+                        const float qu = R.au == 0 ? qx : (R.au == 1 ? qy : zq);
+                        const float qn = R.an == 0 ? qx : (R.an == 1 ? qy : zq);
+                        const float qw = R.dims == 3 ? (R.aw == 0 ? qx : (R.aw == 1 ? qy : zq)) : 0.f;
+                        ok = box_blocks_all(R, __ldg(&gb[2 * cand]), __ldg(&gb[2 * cand + 1]), qu, qn, qw);
+                        pre_tests = 4;
+                    }
                 }
+                const unsigned m = __ballot_sync(kFull, ok);
+                full = c < 5 && ((m >> (4 * c)) & 0xFu) == 0xFu;
+                if (full && corner == 0 && c != 0)
+                    blockers[R.blk_base + tile_pos] = cand;
             }
             pre_blocked = __syncthreads_or(full) != 0;
         }
