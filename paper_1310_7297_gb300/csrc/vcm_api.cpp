@@ -589,13 +589,17 @@ namespace {
 // viewpoints of expensive tiles, larger tiles spread the cull (16 x 8 was
 // 2 % slower on the 3D workload and the 100,000-box scene, 4 % on the
 // 256-request mix; 32 x 8 and 32 x 16 were 40-90 % slower, 8 x 8 18 %).
+// 448 staged boxes: at 6 and 7 blocks per SM, less shared memory leaves more
+// L1 for the tile kernel's spilled registers (against 512: 100,000-box
+// step -0.5 %, 5,000-box step -2.1 %, 256-request batch -0.4 %; 1,024 was
+// 28 % slower on the 100,000-box scene).
 vcm_tune default_tune()
 {
     vcm_tune t;
     t.tile_x = 16;
     t.tile_y = 16;
     t.patch_k = 8;
-    t.box_cap = 512;
+    t.box_cap = 448;
     return t;
 }
 
@@ -2582,7 +2586,7 @@ vcm_status vcm_autotune(vcm_ctx *ctx, const vcm_request *samples, uint32_t n, vc
         CUDA_TRY(cudaEventCreate(&e0));
         CUDA_TRY(cudaEventCreate(&e1));
         const uint32_t tiles[][2] = {{8, 4}, {8, 8}, {16, 8}, {32, 8}, {16, 16}};
-        const uint32_t caps[] = {512, 1024, 2048};
+        const uint32_t caps[] = {256, 448, 768};
         // Rows per pass stay automatic: a batch whose classes used different
         // row counts would keep several sweep variants hot at once, a cost
         // that timing one class at a time does not see (the kernel is
