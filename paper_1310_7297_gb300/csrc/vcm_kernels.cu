@@ -1922,39 +1922,80 @@ __global__ void __launch_bounds__(256) k_recolor_measure(const DevRequest *__res
 // colors
 // ---------------------------------------------------------------------------
 
+// Color of one value (Def. 1 normalisation): level 0 for v = 0, else
+// 1 + floor((L - 1) v / v_ref) capped at L - 1; `edge` marks a value within
+// 1e-5 of an interior bin edge.
+__device__ __forceinline__ unsigned char quantise_one(float v, float vref, int L, bool &edge)
+{
+    unsigned char c = 0;
+    edge = false;
+    if (v > 0.f && vref > 0.f) {
+        const float x = (float)(L - 1) * v / vref;
+        const int f = (int)floorf(x);
+        c = (unsigned char)(1 + min(L - 2, f));
+        const float r = rintf(x);
+        edge = r >= 1.f && r <= (float)(L - 2) && fabsf(x - r) <= 1e-5f * x;
+    }
+    return c;
+}
+
+// Four consecutive viewpoints per thread: one 16-byte load of values and one
+// 4-byte store of colors when the four belong to one request and both
+// addresses are aligned, else one at a time.
 __global__ void k_quantise(const DevRequest *__restrict__ reqs, const long long *__restrict__ vp_prefix,
                            int n_req, long long total)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; 4 * g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long i0 = 4 * g;
         int lo_r = 0, hi_r = n_req - 1;
         while (lo_r < hi_r) {
             int mid = (lo_r + hi_r + 1) >> 1;
-            if (vp_prefix[mid] <= i)
+            if (vp_prefix[mid] <= i0)
                 lo_r = mid;
             else
                 hi_r = mid - 1;
         }
         const DevRequest &R = reqs[lo_r];
-        const long long local = i - vp_prefix[lo_r];
+        const long long local0 = i0 - vp_prefix[lo_r];
+        const long long n_vp = vp_prefix[lo_r + 1] - vp_prefix[lo_r];
         const float vref = R.v_ref_given > 0.f ? R.v_ref_given : __uint_as_float(R.stats->vmax_bits);
-        const float v = R.v_out[local];
         const int L = R.levels;
-        unsigned char c = 0;
-        bool edge = false;
-        if (v > 0.f && vref > 0.f) {
-            const float x = (float)(L - 1) * v / vref;
-            const int f = (int)floorf(x);
-            c = (unsigned char)(1 + min(L - 2, f));
-            const float r = rintf(x);
-            edge = r >= 1.f && r <= (float)(L - 2) && fabsf(x - r) <= 1e-5f * x;
-        }
-        if (R.color_out && IN_BOUNDS(local, (long long)R.nx * R.ny * R.nl, R.stats))
-            R.color_out[local] = c;
-        if (edge)   // rare; lanes of one warp may belong to different requests
-            atomicAdd(&R.stats->edge_cells, 1u);
-        if (local == 0)
+        if (local0 == 0)
             R.stats->v_ref = vref;
+        const float *vsrc = R.v_out + local0;
+        unsigned char *cdst = R.color_out ? R.color_out + local0 : nullptr;
+        if (local0 + 4 <= n_vp && (reinterpret_cast<uintptr_t>(vsrc) & 15u) == 0 &&
+            (reinterpret_cast<uintptr_t>(cdst) & 3u) == 0) {
+            const float4 v4 = *reinterpret_cast<const float4 *>(vsrc);
+            bool e0, e1, e2, e3;
+            const unsigned c = (unsigned)quantise_one(v4.x, vref, L, e0) |
+                               ((unsigned)quantise_one(v4.y, vref, L, e1) << 8) |
+                               ((unsigned)quantise_one(v4.z, vref, L, e2) << 16) |
+                               ((unsigned)quantise_one(v4.w, vref, L, e3) << 24);
+            if (cdst && IN_BOUNDS(local0 + 3, (long long)R.nx * R.ny * R.nl, R.stats))
+                *reinterpret_cast<unsigned *>(cdst) = c;
+            const unsigned n_edge = (unsigned)e0 + (unsigned)e1 + (unsigned)e2 + (unsigned)e3;
+            if (n_edge)   // rare; lanes of one warp may belong to different requests
+                atomicAdd(&R.stats->edge_cells, n_edge);
+            continue;
+        }
+        // one at a time: the group's last viewpoints may start the next requests
+        for (long long i = i0; i < i0 + 4 && i < total; ++i) {
+            while (lo_r + 1 < n_req && vp_prefix[lo_r + 1] <= i)
+                ++lo_r;
+            const DevRequest &Q = reqs[lo_r];
+            const long long local = i - vp_prefix[lo_r];
+            const float qref = Q.v_ref_given > 0.f ? Q.v_ref_given : __uint_as_float(Q.stats->vmax_bits);
+            bool edge;
+            const unsigned char c = quantise_one(Q.v_out[local], qref, Q.levels, edge);
+            if (Q.color_out && IN_BOUNDS(local, (long long)Q.nx * Q.ny * Q.nl, Q.stats))
+                Q.color_out[local] = c;
+            if (edge)
+                atomicAdd(&Q.stats->edge_cells, 1u);
+            if (local == 0)
+                Q.stats->v_ref = qref;
+        }
     }
 }
 
@@ -2141,7 +2182,7 @@ cudaError_t launch_quantise(const DevRequest *d_reqs, const long long *d_vp_pref
 {
     if (total_vp <= 0)
         return cudaSuccess;
-    long long blocks = (total_vp + 255) / 256;
+    long long blocks = ((total_vp + 3) / 4 + 255) / 256;   // four viewpoints per thread
     if (blocks > 152 * 16)
         blocks = 152 * 16;
     k_quantise<<<(int)blocks, 256, 0, stream>>>(d_reqs, d_vp_prefix, n_req, total_vp);
