@@ -14,7 +14,10 @@ constexpr int kWarps = 4;                 // warps per block of the tile kernel
 constexpr int kThreads = kWarps * 32;
 constexpr int kPassCap = 2 * kThreads;       // cells listed per round of the grid walk
 constexpr int kDistClasses = 128;            // distance classes of the candidate counting sort
-constexpr int kTileCheckMinPatches = 1024;   // launches whose requests all have this many use the tile check
+// Launches whose requests all have this many patches use the whole-tile
+// check (and the recorded-blocker pre-check): from 512, the 5,000-box step
+// with 32 x 16 patches went 0.319 -> 0.305 ms (the bar was 1,024).
+constexpr int kTileCheckMinPatches = 512;
 constexpr int kMaxPlanes = 32;            // separating planes kept per tile hull
 constexpr float kBand = 1e-6f;            // FP32 slab margin re-decided in FP64
 constexpr int kMaxBoxCap = 5000;          // candidate boxes a tile stages in shared memory
