@@ -726,7 +726,7 @@ def test_recolor_argument_errors(ctx):
 
 @pytest.mark.parametrize("case", ["two_sided", "fov_strict", "plain_bits"])
 def test_many_patch_requests_take_the_whole_tile_check(ctx, case):
-    """Requests of >= 1,024 patches run the tile kernel's instantiation with
+    """Requests of >= 512 patches run the tile kernel's instantiation with
     the whole-tile check (and, when two-sided or coned, the one with both);
     values, bits and colors still match the oracle."""
     from paper_1310_7297_gb300 import VCM_STRICT, VCM_TWO_SIDED
