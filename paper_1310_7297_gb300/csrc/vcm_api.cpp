@@ -347,7 +347,7 @@ void fill_shape(const Canon &c, const vcm_tune &t, DevRequest &d)
         k = 8;   // the tile kernel sweeps these requests with its 8-row variant
     d.k_rows = k;
     d.row_passes = (c.nw + d.groups * k - 1) / (d.groups * k);
-    // Work sharing: chunks of 16 open viewpoints, published from a tile
+    // Work sharing: chunks of 32 open viewpoints, published from a tile
     // with at least 8 open.  Smaller chunks for requests with many patches
     // (about the same work per chunk) were slower: each chunk stages its
     // owner's candidate list again (100,000-box scene, 64 x 32 patches:

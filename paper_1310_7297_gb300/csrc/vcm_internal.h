@@ -44,7 +44,11 @@ constexpr int kClaimRounds = 4096;        // bounded retries of a spill-region c
 //   blocker[kBlockerCap]             per tile position of each request (whole-tile-check
 //                                    launches): a box id that blocked a tile there, or -1
 // A tile whose publication would pass a cap keeps its viewpoints.
-constexpr int kChunkVp = 16;
+// 32 viewpoints per chunk: a block's 4 warps wait at the chunk's end for the
+// slowest viewpoint, and more viewpoints per chunk spread that wait
+// (100,000-box step 3.50 -> 3.38 ms against 16; 64: 3.44, and the 5,000-box
+// step +7 %; 8: +5 %).
+constexpr int kChunkVp = 32;
 constexpr int kMinPublish = 8;
 // Longer lists stay with their tile (the 100,000-box scene, lists of ~180
 // boxes on average: 6.44 ms with this limit, 6.71 ms without it) unless the
