@@ -232,8 +232,8 @@ typedef struct {
  * of admitted requests, the occlusion bits kept for recolouring
  * (VCM_CACHE_BITS), and the scratch of the scheduler's execution slots.
  * A slot's scratch is a descriptor buffer, a spill list of n_boxes ints per
- * block that can be resident (about 304 MB per slot for 100,000 boxes on
- * 152 SMs) and a 53 MB work buffer through which the blocks of a launch
+ * block that can be resident (about 365 MB per slot for 100,000 boxes on
+ * 152 SMs) and a 74 MB work buffer through which the blocks of a launch
  * share the open viewpoints of expensive tiles; it is allocated when the
  * slot first runs a launch that needs it and kept.  The direct path
  * (vcm_compute, vcm_compute_batch, vcm_recolor) has scratch of its own,
