@@ -338,6 +338,26 @@ vcm_status vcm_get_memory(vcm_ctx *ctx, vcm_memory *out);
  * running request uses. */
 vcm_status vcm_cache_clear(vcm_ctx *ctx);
 
+/* Per-request metric lines and latency percentiles of the asynchronous
+ * path (a serving aid; the paper reports only total times and error
+ * percentages).  With a path, every request whose scheduler launch
+ * completes appends one JSON object, on a line of its own, to that file:
+ * ticket, status (0 or the request's vcm_status), latency_ms, queue_ms,
+ * launch_ms, device_ms, chain_ms, group_size, launch_form, viewpoints,
+ * patches, segments, and the counters of vcm_stats (slab_tests,
+ * corner_tests, rechecked, edge_cells, shortcut_viewpoints,
+ * shared_viewpoints, v_ref).  The scheduler's waiter threads write the
+ * lines after each launch, outside the context lock, and flush the file.
+ * The file is opened for appending; NULL closes it.  VCM_E_ARG if it cannot
+ * be opened. */
+vcm_status vcm_set_request_log(vcm_ctx *ctx, const char *path);
+
+/* Latency (submit to completion) percentiles, nearest rank, over the last
+ * 4,096 requests the scheduler completed without error, and how many it has
+ * completed since the context was created.  p50 and p99 are 0 before the
+ * first. */
+vcm_status vcm_latency_summary(vcm_ctx *ctx, double *p50_ms, double *p99_ms, uint64_t *completed);
+
 /* Host-side fault injection, for testing how failures surface (nothing
  * here faults or stalls the GPU).
  * VCM_INJECT_SPILL_BUSY: the next `count` launches of the scheduler run one

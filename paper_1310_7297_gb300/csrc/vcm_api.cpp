@@ -550,6 +550,13 @@ struct vcm_ctx {
     std::vector<std::shared_ptr<CacheEntry>> cache;
     size_t cache_bytes = 0;
     uint64_t cache_clock = 0;
+    // per-request metric lines (vcm_set_request_log) and the latencies of the
+    // last kLatencyRing completed requests (vcm_latency_summary)
+    std::mutex log_mu;
+    FILE *req_log = nullptr;        // guarded by log_mu
+    std::atomic<bool> log_on{false};
+    std::vector<double> lat_ring;   // guarded by mu
+    uint64_t lat_done = 0;
 };
 
 namespace {
@@ -1146,6 +1153,41 @@ void cache_clear(vcm_ctx *ctx)
     }
 }
 
+constexpr size_t kLatencyRing = 4096;
+
+// A completed request: its latency into the ring (when it succeeded) and,
+// with the request log on, its metric line (called with ctx->mu held).
+void note_completion(vcm_ctx *ctx, const Ticket &t, std::string &lines)
+{
+    const double lat = std::chrono::duration<double, std::milli>(t.t_done - t.t_submit).count();
+    if (t.state == T_DONE) {
+        if (ctx->lat_ring.size() < kLatencyRing)
+            ctx->lat_ring.push_back(lat);
+        else
+            ctx->lat_ring[ctx->lat_done % kLatencyRing] = lat;
+        ctx->lat_done++;
+    }
+    if (!ctx->log_on.load(std::memory_order_relaxed))
+        return;
+    const Canon &c = t.canon;
+    const vcm_stats z{};
+    const vcm_stats &st = (t.h_stats && t.state == T_DONE) ? *t.h_stats : z;
+    char buf[768];
+    std::snprintf(buf, sizeof buf,
+                  "{\"ticket\": %llu, \"status\": %d, \"latency_ms\": %.6f, \"queue_ms\": %.6f, "
+                  "\"launch_ms\": %.6f, \"device_ms\": %.6f, \"chain_ms\": %.6f, \"group_size\": %u, "
+                  "\"launch_form\": %u, \"viewpoints\": %lld, \"patches\": %d, \"segments\": %llu, "
+                  "\"slab_tests\": %llu, \"corner_tests\": %llu, \"rechecked\": %llu, \"edge_cells\": %u, "
+                  "\"shortcut_viewpoints\": %llu, \"shared_viewpoints\": %llu, \"v_ref\": %.9g}\n",
+                  (unsigned long long)t.id, t.state == T_DONE ? 0 : (int)t.err, lat,
+                  std::chrono::duration<double, std::milli>(t.t_launch - t.t_submit).count(), t.launch_ms,
+                  t.device_ms, t.chain_ms, t.group_size, t.form, (long long)c.n_vp, c.P,
+                  (unsigned long long)c.n_vp * (unsigned long long)c.P, st.slab_tests, st.corner_tests,
+                  st.rechecked, st.edge_cells, st.shortcut_viewpoints, st.shared_viewpoints, (double)st.v_ref);
+    lines += buf;
+}
+
+
 // Completion of a slot's launches.  CUDA host callbacks are not used: a
 // callback that takes the context lock can deadlock against a thread that
 // holds the lock inside a call that implicitly synchronises the device
@@ -1212,6 +1254,20 @@ void slot_waiter(vcm_ctx *ctx, Slot *s)
         s->busy = false;
         ctx->running_groups--;
         ctx->cv.notify_all();
+        std::string lines;
+        for (auto &t : group)
+            note_completion(ctx, *t, lines);
+        if (!lines.empty()) {
+            lk.unlock();
+            {
+                std::lock_guard<std::mutex> g(ctx->log_mu);
+                if (ctx->req_log) {
+                    fputs(lines.c_str(), ctx->req_log);
+                    fflush(ctx->req_log);
+                }
+            }
+            lk.lock();
+        }
     }
 }
 
@@ -1804,6 +1860,8 @@ void vcm_ctx_destroy(vcm_ctx *ctx)
     free_scene(ctx);
     if (ctx->aux)
         cudaStreamDestroy(ctx->aux);
+    if (ctx->req_log)
+        fclose(ctx->req_log);
     delete ctx;
 }
 
@@ -2267,6 +2325,49 @@ vcm_status vcm_cache_clear(vcm_ctx *ctx)
         cache_clear(ctx);
     }
     ctx->cv.notify_all();   // freed memory may admit queued requests
+    return VCM_OK;
+}
+
+vcm_status vcm_set_request_log(vcm_ctx *ctx, const char *path)
+{
+    vcm_status st = validate_ctx(ctx);
+    if (st != VCM_OK)
+        return st;
+    FILE *f = nullptr;
+    if (path) {
+        f = std::fopen(path, "a");
+        if (!f)
+            return fail(VCM_E_ARG, "cannot open %s for appending", path);
+    }
+    std::lock_guard<std::mutex> g(ctx->log_mu);
+    if (ctx->req_log)
+        std::fclose(ctx->req_log);
+    ctx->req_log = f;
+    ctx->log_on.store(f != nullptr, std::memory_order_relaxed);
+    return VCM_OK;
+}
+
+vcm_status vcm_latency_summary(vcm_ctx *ctx, double *p50_ms, double *p99_ms, uint64_t *completed)
+{
+    vcm_status st = validate_ctx(ctx);
+    if (st != VCM_OK)
+        return st;
+    if (!p50_ms || !p99_ms || !completed)
+        return fail(VCM_E_ARG, "NULL argument");
+    std::vector<double> lat;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        lat = ctx->lat_ring;
+        *completed = ctx->lat_done;
+    }
+    *p50_ms = *p99_ms = 0.0;
+    if (lat.empty())
+        return VCM_OK;
+    std::sort(lat.begin(), lat.end());
+    // nearest rank: the smallest latency with at least q of the requests at or below it
+    auto rank = [&](double q) { return lat[std::max<size_t>(1, (size_t)std::ceil(q * lat.size())) - 1]; };
+    *p50_ms = rank(0.50);
+    *p99_ms = rank(0.99);
     return VCM_OK;
 }
 

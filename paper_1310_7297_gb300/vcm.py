@@ -33,7 +33,8 @@ EXPORTS = ["vcm_ctx_create", "vcm_ctx_destroy", "vcm_last_error", "vcm_scene_loa
            "vcm_scene_save", "vcm_build", "vcm_compute", "vcm_submit", "vcm_submit_batch", "vcm_poll",
            "vcm_result_get", "vcm_result_release", "vcm_cancel", "vcm_set_slots", "vcm_compute_batch",
            "vcm_autotune", "vcm_set_tune", "vcm_get_tune", "vcm_set_timing_events", "vcm_compute_static",
-           "vcm_recolor", "vcm_get_memory", "vcm_inject", "vcm_cache_clear"]
+           "vcm_recolor", "vcm_get_memory", "vcm_inject", "vcm_cache_clear", "vcm_set_request_log",
+           "vcm_latency_summary"]
 
 
 class _DeviceArray:
@@ -392,6 +393,17 @@ class Context:
 
     def vcm_cache_clear(self):
         return self._ck(self.L.vcm_cache_clear(self.h))
+
+    def vcm_set_request_log(self, path):
+        """Append one JSON metric line per completed request to `path` (None closes it)."""
+        arg = None if path is None else os.fsencode(path)
+        return self._ck(self.L.vcm_set_request_log(self.h, ctypes.c_char_p(arg)))
+
+    def vcm_latency_summary(self):
+        """(p50_ms, p99_ms, completed) over the scheduler's recent requests."""
+        p50, p99, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        self._ck(self.L.vcm_latency_summary(self.h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(n)))
+        return p50.value, p99.value, n.value
 
     # tuning -------------------------------------------------------------------
     def vcm_autotune(self, samples):

@@ -282,3 +282,44 @@ def test_gaze_change_is_served_from_cached_bits(scene_reqs):
         assert m["cache_entries"] == 0 and m["cached_bits"] == 0
     finally:
         ctx.close()
+
+
+def test_request_log_and_latency_summary(scene_reqs, tmp_path):
+    """Each request whose scheduler launch completes appends one JSON line
+    with its timings and device counters, which match what vcm_result_get
+    reports; the latency summary covers the completed requests."""
+    import json
+
+    scene, reqs = scene_reqs
+    ctx = _ctx(scene)
+    path = tmp_path / "requests.jsonl"
+    try:
+        assert ctx.vcm_latency_summary() == (0.0, 0.0, 0)
+        ctx.vcm_set_request_log(str(path))
+        tickets = [ctx.vcm_submit(r) for r in reqs]
+        got = {}
+        for t in tickets:
+            assert ctx.vcm_poll(t, -1) == 0
+            _, _, _, st = ctx.vcm_result_get(t, copy=False)
+            got[t] = st
+            ctx.vcm_result_release(t)
+        ctx.vcm_set_request_log(None)   # closes the file
+        lines = [json.loads(x) for x in path.read_text().splitlines()]
+        assert sorted(x["ticket"] for x in lines) == sorted(tickets)
+        for x in lines:
+            st = got[x["ticket"]]
+            assert x["status"] == 0
+            assert x["segments"] == x["viewpoints"] * x["patches"] == st["segments"]
+            for k in ("slab_tests", "corner_tests", "rechecked", "edge_cells", "shortcut_viewpoints",
+                      "shared_viewpoints"):
+                assert x[k] == st[k], k
+            assert abs(x["latency_ms"] - st["latency_ms"]) < 1e-3
+            assert abs(x["device_ms"] - st["device_ms"]) < 1e-3
+            assert 0.0 <= x["chain_ms"] <= x["device_ms"] + 1e-6
+        p50, p99, n = ctx.vcm_latency_summary()
+        lat = sorted(got[t]["latency_ms"] for t in tickets)
+        assert n == len(tickets)
+        assert lat[0] - 1e-6 <= p50 <= p99 <= lat[-1] + 1e-6
+    finally:
+        ctx.close()
+
